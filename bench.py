@@ -1,0 +1,411 @@
+"""Benchmark: saturated vs as-written FP64 compressible-flow RHS at 256^3 on GB300.
+
+One step = one call of `acs_rhs_saturated` over the 256^3 interior (+2 halo) of the
+seeded synthetic field, inputs resident in HBM (703 MB in + 671 MB out, both larger than
+the 129 MB L2, so no flush is needed between steps). The as-written form
+(`acs_rhs_plain`) is timed on the same input in the same run, and so are both forms of the
+25-point star stencil at 384^3, as context.
+
+Printed: one JSON line (rank 0). `value` = Gpoint-updates/s of the saturated form summed
+over ranks (each rank runs its own replica: no collective on the data path).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "Gpoint-updates/s & HBM GB/s, saturated vs as-written, 256^3 FP64, ≤1e-12 rel"
+UNIT = "Gpoint-updates/s"
+N_RHS = 256
+N_STAR = 384
+
+# FP64-pipe operations per interior point of the saturated RHS, from its expression DAG
+# (FMA, add, mul each one pipe operation): per point 21 for the fluxes (3 Newton FMAs of
+# the reciprocal, 3 velocities, 2 for |m.v|, 2 for P, E+P, 3 diagonal, 3 off-diagonal,
+# 3 energy) + 5 components x 19 (3 differences, 3 for the scaled flux sum, 10 for S2 and S1,
+# 2 for S2 - 4 S1 + 18 U, 1 final FMA) = 116. The star stencil: 1 + 12 x 2 + 1 = 26.
+DP_OPS_PER_POINT = {"rhs_saturated": 116, "star_saturated": 26}
+# Peak FP64-pipe rate: 2 operations / clock / SM (nominal 1.25 TFLOP/s of FMA at 2070 MHz on
+# 152 SMs: 1.25e12 / 2 / 152 / 2.07e9 = 1.99), i.e. 2 * 152 * 2.07e9 = 629.3 G op/s.
+SMS = 152
+SM_MAX_MHZ = 2070.0
+DP_PEAK_GOPS = 2 * SMS * SM_MAX_MHZ / 1000.0
+
+# DRAM bytes per launch measured by ncu for the current kernel source (keyed by the SHA-256 of
+# the files that define it); a changed kernel reports null until it is profiled again.
+NCU_TRAFFIC = {
+    # ncu --set full of rhs_saturated_kernel<32,8> at 192^3 (564 MB DRAM read+write), scaled by
+    # points to one 256^3 launch; summary in profiles/rhs_saturated_192cubed_ncu_full.md.
+    "31af6eec0a8e26b3": 1336558175,
+}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("rhs_saturated.cu", "acs_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2306_13002_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 100 ms; keeps those inside [t0, t1]."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), [x.strip() for x in line.split(",")]))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float) -> dict:
+        rows = [s for (t, s) in self.samples if t0 <= t <= t1 and len(s) >= 9]
+        if not rows:
+            rows = [s for (_, s) in self.samples if len(s) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(U: np.ndarray, budget_s: float = 12.0) -> dict:
+    """The oracle (as-written FP64 loop nest, gcc) on a bounded z-slab sample of the same field."""
+    import oracle
+    threads = os.cpu_count() or 1
+    if not oracle.has_openmp():
+        threads = 1
+    n = U.shape[-1] - 4
+    t = time.perf_counter()
+    oracle.rhs(U, k_range=(0, 1), threads=threads)
+    t1 = max(time.perf_counter() - t, 1e-4)
+    planes = int(max(1, min(n, budget_s / t1)))
+    t = time.perf_counter()
+    oracle.rhs(U, k_range=(0, planes), threads=threads)
+    dt = time.perf_counter() - t
+    pts = planes * n * n
+    return {"value": pts / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"as-written RHS oracle on {planes} of {n} z-planes of the {n}^3 field ({pts} points, {dt:.1f} s)"}
+
+
+def run_reference(args) -> None:
+    """Reference arm: the CPU oracle, as it stands, on host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2306_13002_gb300 import inputs
+    oracle.build()
+    U = inputs.rhs_field(N_RHS, halo=2, seed=inputs.SEED_RHS_LARGE)
+    threads = os.cpu_count() or 1
+    if not oracle.has_openmp():
+        threads = 1
+    t = time.perf_counter()
+    oracle.rhs(U, k_range=(0, 1), threads=threads)
+    t1 = max(time.perf_counter() - t, 1e-4)
+    total = max(1, args.steps + args.warmup)
+    planes = int(max(1, min(N_RHS, 120.0 / total / t1)))
+    times = []
+    for s in range(total):
+        k0 = (s * planes) % (N_RHS - planes + 1)
+        t = time.perf_counter()
+        oracle.rhs(U, k_range=(k0, k0 + planes), threads=threads)
+        dt = time.perf_counter() - t
+        if s >= args.warmup:
+            times.append(dt)
+    pts = planes * N_RHS * N_RHS
+    mean = sum(times) / len(times)
+    value = pts / mean / 1e9
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "rhs_as_written_oracle_256^3_fp64", "grid": [N_RHS] * 3, "halo": 2,
+                   "sample_planes_per_step": planes},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{planes} z-planes of the {N_RHS}^3 field per step ({pts} points)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def time_launches(torch, fn, steps: int, stream) -> tuple[float, float]:
+    """Per-launch CUDA-event durations on `stream`; returns (mean launch ms, region ms)."""
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    for s in range(steps):
+        starts[s].record(stream)
+        fn()
+        ends[s].record(stream)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    per = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    return sum(per) / len(per), r0.elapsed_time(r1)
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-stencil", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the as-written timing")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end timing")
+    ap.add_argument("--n", type=int, default=N_RHS, help="RHS interior side (256 is the benchmark workload)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    args.steps = max(args.steps, 1)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2306_13002_gb300 import binding, inputs
+    from paper_2306_13002_gb300 import build as acs_build
+    if rank == 0:
+        acs_build.build()
+    if dist:
+        dist.barrier()
+    binding.lib()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x: float) -> float:
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    n = args.n
+    U_host = inputs.rhs_field(n, halo=2, seed=inputs.SEED_RHS_LARGE + rank)
+    U_pin = torch.from_numpy(U_host).pin_memory()
+    R_pin = torch.empty((5, n, n, n), dtype=torch.float64).pin_memory()
+    U = U_pin.to("cuda")
+    R = torch.empty((5, n, n, n), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    points = n ** 3
+    in_bytes = U.numel() * 8
+    out_bytes = R.numel() * 8
+
+    sat = lambda: binding.acs_rhs_saturated(U, R, stream=stream)  # noqa: E731
+    plain = lambda: binding.acs_rhs_plain(U, R, stream=stream)  # noqa: E731
+
+    for _ in range(args.warmup):
+        sat()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    launch_ms, region_ms = time_launches(torch, sat, args.steps, stream)
+    t1 = time.time()
+    torch.cuda.synchronize()
+    barrier()
+    region_ms = max_over_ranks(region_ms)
+    launch_ms = max_over_ranks(launch_ms)
+    ms_per_step = region_ms / args.steps
+    value = sum_over_ranks(points / (ms_per_step * 1e-3) / 1e9)
+
+    # Quick parity spot check of the timed output (plane 0 and the middle plane).
+    parity = None
+    if rank == 0:
+        import oracle
+        worst = 0.0
+        Rh = R.cpu().numpy()
+        for k in (0, n // 2, n - 1):
+            ref = oracle.rhs(U_host, k_range=(k, k + 1), threads=os.cpu_count() or 1)[:, k]
+            worst = max(worst, float(np.max(np.abs(Rh[:, k] - ref) / (1e-12 * np.abs(ref) + 1e-14))))
+        parity = {"planes": [0, n // 2, n - 1], "max_err_over_tolerance": worst}
+
+    # As-written form on the same input.
+    as_written = None
+    if not args.no_plain:
+        for _ in range(2):
+            plain()
+        torch.cuda.synchronize()
+        plain_steps = max(3, min(args.steps, 40))
+        barrier()
+        plain_launch_ms, plain_region_ms = time_launches(torch, plain, plain_steps, stream)
+        barrier()
+        plain_ms = max_over_ranks(plain_region_ms) / plain_steps
+        plain_value = sum_over_ranks(points / (plain_ms * 1e-3) / 1e9)
+        as_written = {"value": plain_value, "ms_per_step": plain_ms, "launch_ms": plain_launch_ms,
+                      "speedup_saturated_over_as_written": plain_ms / ms_per_step}
+
+    # End to end through the public API: pinned host U -> device, kernel, device R -> host.
+    def e2e_step():
+        U.copy_(U_pin, non_blocking=True)
+        binding.acs_rhs_saturated(U, R, stream=stream)
+        R_pin.copy_(R, non_blocking=True)
+
+    e2e = None
+    if not args.no_e2e:
+        e2e_step()
+        torch.cuda.synchronize()
+        e2e_steps = max(3, min(args.steps, 20))
+        barrier()
+        _, e2e_region = time_launches(torch, e2e_step, e2e_steps, stream)
+        barrier()
+        e2e_ms = max_over_ranks(e2e_region) / e2e_steps
+        e2e_value = sum_over_ranks(points / (e2e_ms * 1e-3) / 1e9)
+        e2e = {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_ms, "h2d_bytes_per_step": in_bytes,
+               "d2h_bytes_per_step": out_bytes}
+
+    if sampler:
+        sampler.stop()
+        clocks = sampler.summary(t0, t1)
+    else:
+        clocks = None
+
+    # Star stencil, both forms, as context (one replica per rank, rank 0 reports).
+    stencil = None
+    if not args.no_stencil:
+        del U, R
+        torch.cuda.empty_cache()
+        m = N_STAR
+        u_np, a_np = inputs.stencil_fields(m, halo=4, seed=inputs.SEED_STENCIL)
+        u = torch.from_numpy(u_np).to("cuda")
+        a = torch.from_numpy(a_np).to("cuda")
+        out = torch.empty((m, m, m), dtype=torch.float64, device="cuda")
+        ssat = lambda: binding.acs_stencil_saturated(u, a, out, stream=stream)  # noqa: E731
+        splain = lambda: binding.acs_stencil_plain(u, a, out, stream=stream)  # noqa: E731
+        res = {}
+        for name, fn in (("saturated", ssat), ("as_written", splain)):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            lm, rm = time_launches(torch, fn, max(3, min(args.steps, 50)), stream)
+            ms = rm / max(3, min(args.steps, 50))
+            res[name] = {"ms": ms, "gpts": m ** 3 / (ms * 1e-3) / 1e9}
+        star_bytes = 8 * (2 * (m + 8) ** 3 + m ** 3)
+        res["speedup"] = res["as_written"]["ms"] / res["saturated"]["ms"]
+        res["saturated"]["fp64_gops"] = DP_OPS_PER_POINT["star_saturated"] * m ** 3 / (res["saturated"]["ms"] * 1e-3) / 1e9
+        res["saturated"]["hbm_gbs_algorithmic"] = star_bytes / (res["saturated"]["ms"] * 1e-3) / 1e9
+        stencil = {"grid": [m] * 3, "halo": 4, **res}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    peaks = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    algo_bytes = in_bytes + out_bytes
+    achieved_ops = DP_OPS_PER_POINT["rhs_saturated"] * points / (launch_ms * 1e-3) / 1e9
+    traffic = NCU_TRAFFIC.get(kernel_source_hash())
+    result = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"rhs_saturated_{n}^3_fp64", "grid": [n] * 3, "halo": 2, "gamma": 1.4, "eps": 0.25,
+                   "tile": "32x8, default z-chunk", "l2": f"inputs larger than L2 ({in_bytes / 1e6:.0f} MB in, {out_bytes / 1e6:.0f} MB out)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "alu", "achieved": achieved_ops, "peak": DP_PEAK_GOPS, "unit": "G FP64-pipe op/s",
+                     "frac": achieved_ops / DP_PEAK_GOPS, "traffic": traffic,
+                     "peak_source": "derived: 2 FP64 op/clk/SM x 152 SMs x 2070 MHz"},
+        "hbm": {"algorithmic_bytes_per_launch": algo_bytes, "achieved_gbs": algo_bytes / (launch_ms * 1e-3) / 1e9,
+                "peak_gbs": hbm_peak, "frac": algo_bytes / (launch_ms * 1e-3) / 1e9 / hbm_peak,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6800"},
+        "as_written": as_written,
+        "kernel_launch_ms": launch_ms,
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "parity": parity,
+        "stencil_384": stencil,
+    }
+    if not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(U_host)
+    print(json.dumps(result))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

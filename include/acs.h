@@ -1,0 +1,148 @@
+/*
+ * acs.h - C ABI of the GB300 (sm_103a) stencil library.
+ *
+ * The library evaluates two FP64 3D stencil loop bodies, each in two forms:
+ *
+ *   as-written ("plain")  the loop body exactly as a directive-style code states it: one
+ *                         thread per point, every statement evaluated on its own with its
+ *                         own loads and its own recomputation of shared subexpressions;
+ *   saturated             the same values after the rewrites of equality saturation
+ *                         (paper Sec. V-A, Table I: FMA formation, commutativity,
+ *                         associativity, constant folding; Sec. IV-B: extraction with
+ *                         common subexpressions counted once) and "bulk load"
+ *                         (Sec. VI-B: every load moved to the earliest point, ahead of the
+ *                         arithmetic), here extended across neighbouring iterations.
+ *
+ * Both forms compute the as-written value up to floating-point rounding; equality
+ * saturation preserves semantics (Sec. IV). The two loop bodies are:
+ *
+ *  (1) RHS of the 3D compressible Euler equations with 4th-order artificial dissipation,
+ *      the halo-CFD kernel shape of NPB BT/LU/SP (Table II). Conserved variables
+ *      U = (rho, m_x, m_y, m_z, E), ideal gas with ratio gamma. At each interior point p
+ *      and component c:
+ *        R_c(p) = - sum_d (F_{d,c}(p+e_d) - F_{d,c}(p-e_d)) / (2 h_d)
+ *                 - eps * sum_d (U_c(p-2e_d) - 4U_c(p-e_d) + 6U_c(p) - 4U_c(p+e_d) + U_c(p+2e_d))
+ *      with v_d = m_d/rho, P = (gamma-1)(E - |m|^2/(2 rho)) and
+ *        F_d = [m_d, m_x v_d + P[d=x], m_y v_d + P[d=y], m_z v_d + P[d=z], (E+P) v_d].
+ *  (2) Variable-coefficient 25-point (radius 4) star stencil, the halo-Jacobi shape of
+ *      SPEC ACCEL ostencil (Table III):
+ *        out(p) = sum_d sum_{o=1..4} c[d][o-1] * a(p) * (u(p+o e_d) - 2u(p) + u(p-o e_d)).
+ *
+ * Conventions common to every entry point
+ *  - All arrays are FP64 in device memory owned by the caller. The library never
+ *    allocates device memory on these paths and keeps no pointer after a call returns.
+ *  - x is the unit-stride axis. Inputs are halo-extended arrays addressed from their
+ *    corner cell: element (i, j, k) of component c of an input is at
+ *        base[c*in_sc + k*in_sz + j*in_sy + i],   0 <= i < nx+2*halo, ...
+ *    and interior point (i, j, k) is extended element (i+halo, j+halo, k+halo).
+ *    Outputs are addressed from interior point (0, 0, 0):
+ *        out[c*out_sc + k*out_sz + j*out_sy + i],  0 <= i < nx, ...
+ *    Only interior points are written; nothing else in the output buffer is touched.
+ *  - Calls are asynchronous on `stream` (NULL = the legacy default stream). Argument
+ *    checks run on the host before any launch; a failed check launches nothing and
+ *    returns a status. Launch failures return ACS_ERR_CUDA. `acs_last_error()` gives a
+ *    human-readable reason for the last failure of the calling thread.
+ *  - Inputs and outputs must not overlap in memory (ACS_ERR_ALIAS).
+ *  - The saturated RHS computes 1/rho with a refined hardware reciprocal estimate for
+ *    normal rho in [2^-1000, 2^1000] and falls back to an IEEE division otherwise.
+ */
+#ifndef ACS_H
+#define ACS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream handle; this is the type behind cudaStream_t. */
+typedef struct CUstream_st *acs_stream;
+
+typedef enum acs_status {
+    ACS_OK = 0,
+    ACS_ERR_INVALID = 1,     /* null pointer, bad size, stride or parameter */
+    ACS_ERR_ALIGN = 2,       /* a pointer or stride breaks an alignment the kernel needs */
+    ACS_ERR_CUDA = 3,        /* a CUDA runtime call or a kernel launch failed */
+    ACS_ERR_UNSUPPORTED = 4, /* valid request that this build does not implement */
+    ACS_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+    ACS_ERR_NOMODEL = 6,     /* no ranker model was supplied where one is required */
+    ACS_ERR_ALIAS = 7,       /* an output overlaps an input */
+    ACS_ERR_WORKSPACE = 8    /* workspace missing or too small */
+} acs_status;
+
+/* Geometry of one grid (see the addressing rules above). */
+typedef struct acs_grid {
+    int nx, ny, nz;                    /* interior points per axis, each >= 1 */
+    int halo;                          /* ghost layers of the inputs on every side */
+    long long in_sy, in_sz, in_sc;     /* input element strides: row, plane, component */
+    long long out_sy, out_sz, out_sc;  /* output element strides: row, plane, component */
+} acs_grid;
+
+/* Physical parameters of the RHS: ratio of specific heats, dissipation weight, spacing. */
+typedef struct acs_rhs_params {
+    double gamma;
+    double eps;
+    double h[3];                       /* grid spacing along x, y, z; each nonzero */
+} acs_rhs_params;
+
+/* Launch shape of a saturated kernel. A NULL tile selects the built-in default. */
+typedef struct acs_tile {
+    int bx;       /* threads (points) along x per block: 16, 32 or 64 */
+    int by;       /* threads (points) along y per block: 4, 8 or 16 */
+    int kchunk;   /* z-planes marched by one block; 0 = pick from the grid size */
+    int flags;    /* reserved, must be 0 */
+} acs_tile;
+
+/*
+ * acs_rhs_plain - as-written RHS, loop body (1) evaluated statement by statement.
+ *   U      input, 5 components, halo >= 2        (read only)
+ *   R      output, 5 components, interior only   (written)
+ *   g      geometry; in_sc and out_sc separate the 5 components
+ *   p      gamma, eps, h
+ * Alignment: 8-byte aligned pointers. Returns ACS_OK or an error status.
+ */
+acs_status acs_rhs_plain(const double *U, double *R, const acs_grid *g, const acs_rhs_params *p,
+                         acs_stream stream);
+
+/*
+ * acs_rhs_saturated - the saturated RHS: per-point fluxes computed once and shared with
+ * the six neighbours, one reciprocal per point, dissipation reassociated as
+ * sum(U at +-2) - 4 sum(U at +-1) + 18 U, FMA throughout, and every plane of U staged in
+ * shared memory ahead of the arithmetic (bulk load). Same arguments as acs_rhs_plain plus
+ *   tile   launch shape or NULL.
+ */
+acs_status acs_rhs_saturated(const double *U, double *R, const acs_grid *g, const acs_rhs_params *p,
+                             const acs_tile *tile, acs_stream stream);
+
+/*
+ * acs_stencil_plain - as-written 25-point star stencil, loop body (2).
+ *   u, a   inputs with the same geometry, halo >= 4 (only a at interior points is read)
+ *   out    output, interior only
+ *   c      12 host doubles, c[4*d + (o-1)] for axis d = 0..2 (x, y, z), offset o = 1..4
+ */
+acs_status acs_stencil_plain(const double *u, const double *a, double *out, const acs_grid *g,
+                             const double *c, acs_stream stream);
+
+/*
+ * acs_stencil_saturated - the saturated star stencil:
+ *   out = a(p) * (C0 u(p) + sum_d sum_o c[d][o] (u(p+o e_d) + u(p-o e_d))),
+ *   C0 = -2 sum c (folded on the host), FMA throughout, u planes staged in shared memory
+ *   and reused by the 9 z-offsets as the block marches along z.
+ */
+acs_status acs_stencil_saturated(const double *u, const double *a, double *out, const acs_grid *g,
+                                 const double *c, const acs_tile *tile, acs_stream stream);
+
+/* Static text for a status code. */
+const char *acs_status_string(acs_status s);
+
+/* Reason for the calling thread's most recent failed call ("" if none). */
+const char *acs_last_error(void);
+
+/* ABI version of this library (major * 100 + minor). */
+int acs_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ACS_H */

@@ -1,0 +1,179 @@
+"""Thin ctypes binding of `libacs.so` (argument marshalling only).
+
+The functions carry the C-ABI names of `include/acs.h`. They accept torch CUDA tensors
+(or any object with `data_ptr()`, `stride()`, `shape`), build the `acs_grid` from the
+tensors' own strides, call the library on the given stream and raise `AcsError` on a
+non-OK status. Every step of the computation runs in the CUDA library; if it is missing,
+loading fails loudly: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libacs.so")
+
+ACS_OK = 0
+STATUS_NAMES = {
+    0: "ACS_OK", 1: "ACS_ERR_INVALID", 2: "ACS_ERR_ALIGN", 3: "ACS_ERR_CUDA", 4: "ACS_ERR_UNSUPPORTED",
+    5: "ACS_ERR_TIMEOUT", 6: "ACS_ERR_NOMODEL", 7: "ACS_ERR_ALIAS", 8: "ACS_ERR_WORKSPACE",
+}
+
+TAYLOR8 = (8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0)
+
+
+class AcsError(RuntimeError):
+    def __init__(self, status: int, func: str, detail: str):
+        self.status = status
+        self.name = STATUS_NAMES.get(status, str(status))
+        super().__init__(f"{func}: {self.name}: {detail}")
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("halo", ctypes.c_int),
+                ("in_sy", ctypes.c_longlong), ("in_sz", ctypes.c_longlong), ("in_sc", ctypes.c_longlong),
+                ("out_sy", ctypes.c_longlong), ("out_sz", ctypes.c_longlong), ("out_sc", ctypes.c_longlong)]
+
+
+class RhsParams(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("eps", ctypes.c_double), ("h", ctypes.c_double * 3)]
+
+
+class Tile(ctypes.Structure):
+    _fields_ = [("bx", ctypes.c_int), ("by", ctypes.c_int), ("kchunk", ctypes.c_int), ("flags", ctypes.c_int)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+EXPORTS = ("acs_rhs_plain", "acs_rhs_saturated", "acs_stencil_plain", "acs_stencil_saturated",
+           "acs_status_string", "acs_last_error", "acs_abi_version")
+
+
+def lib() -> ctypes.CDLL:
+    """Load libacs.so (built by `build.build()` / `__graft_entry__.build()`)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                                   "(run paper_2306_13002_gb300.build.build())")
+            L = ctypes.CDLL(LIB_PATH)
+            p, st = ctypes.c_void_p, ctypes.c_int
+            L.acs_rhs_plain.argtypes = [p, p, ctypes.POINTER(Grid), ctypes.POINTER(RhsParams), p]
+            L.acs_rhs_saturated.argtypes = [p, p, ctypes.POINTER(Grid), ctypes.POINTER(RhsParams),
+                                            ctypes.POINTER(Tile), p]
+            L.acs_stencil_plain.argtypes = [p, p, p, ctypes.POINTER(Grid), ctypes.POINTER(ctypes.c_double), p]
+            L.acs_stencil_saturated.argtypes = [p, p, p, ctypes.POINTER(Grid), ctypes.POINTER(ctypes.c_double),
+                                                ctypes.POINTER(Tile), p]
+            for f in ("acs_rhs_plain", "acs_rhs_saturated", "acs_stencil_plain", "acs_stencil_saturated"):
+                getattr(L, f).restype = st
+            L.acs_status_string.argtypes = [st]
+            L.acs_status_string.restype = ctypes.c_char_p
+            L.acs_last_error.restype = ctypes.c_char_p
+            L.acs_abi_version.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _check(status: int, func: str) -> None:
+    if status != ACS_OK:
+        raise AcsError(status, func, lib().acs_last_error().decode())
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream or None
+        except Exception:  # pragma: no cover
+            return None
+    if isinstance(stream, int):
+        return stream or None
+    return getattr(stream, "cuda_stream", None) or None
+
+
+def _tile(tile) -> ctypes.POINTER(Tile) | None:
+    if tile is None:
+        return None
+    if isinstance(tile, Tile):
+        return ctypes.byref(tile)
+    bx, by, kchunk = (tuple(tile) + (0, 0, 0))[:3]
+    return ctypes.byref(Tile(int(bx), int(by), int(kchunk), 0))
+
+
+def grid_for(inp, out, halo: int, ncomp: int) -> Grid:
+    """acs_grid from an input (halo-extended) and an output tensor's shapes and strides."""
+    if ncomp == 5:
+        _, Z, Y, X = inp.shape
+        isc, isz, isy, isx = inp.stride()
+        osc, osz, osy, osx = out.stride()
+        onz, ony, onx = out.shape[1:]
+    else:
+        Z, Y, X = inp.shape
+        isz, isy, isx = inp.stride()
+        osz, osy, osx = out.stride()
+        isc = osc = 0
+        onz, ony, onx = out.shape
+    if isx != 1 or osx != 1:
+        raise ValueError("x must be the unit-stride axis of input and output")
+    nx, ny, nz = X - 2 * halo, Y - 2 * halo, Z - 2 * halo
+    if (onx, ony, onz) != (nx, ny, nz):
+        raise ValueError(f"output shape {(onz, ony, onx)} does not match the interior {(nz, ny, nx)}")
+    return Grid(nx, ny, nz, halo, isy, isz, isc, osy, osz, osc)
+
+
+def _params(gamma, eps, h) -> RhsParams:
+    return RhsParams(float(gamma), float(eps), (ctypes.c_double * 3)(*[float(v) for v in h]))
+
+
+def acs_rhs_plain(U, R, gamma: float = 1.4, eps: float = 0.25, h=(1.0, 1.0, 1.0), halo: int = 2,
+                  stream=None) -> None:
+    g = grid_for(U, R, halo, 5)
+    pr = _params(gamma, eps, h)
+    _check(lib().acs_rhs_plain(U.data_ptr(), R.data_ptr(), ctypes.byref(g), ctypes.byref(pr),
+                               _stream_ptr(stream)), "acs_rhs_plain")
+
+
+def acs_rhs_saturated(U, R, gamma: float = 1.4, eps: float = 0.25, h=(1.0, 1.0, 1.0), halo: int = 2,
+                      tile=None, stream=None) -> None:
+    g = grid_for(U, R, halo, 5)
+    pr = _params(gamma, eps, h)
+    _check(lib().acs_rhs_saturated(U.data_ptr(), R.data_ptr(), ctypes.byref(g), ctypes.byref(pr), _tile(tile),
+                                   _stream_ptr(stream)), "acs_rhs_saturated")
+
+
+def _coef(c) -> ctypes.Array:
+    if c is None:
+        vals = list(TAYLOR8) * 3
+    else:
+        vals = [float(v) for row in c for v in (row if hasattr(row, "__len__") else [row])]
+    if len(vals) != 12:
+        raise ValueError("stencil coefficients must be 3 x 4")
+    return (ctypes.c_double * 12)(*vals)
+
+
+def acs_stencil_plain(u, a, out, c=None, halo: int = 4, stream=None) -> None:
+    g = grid_for(u, out, halo, 1)
+    if tuple(a.stride()) != tuple(u.stride()) or tuple(a.shape) != tuple(u.shape):
+        raise ValueError("u and a must have the same shape and strides")
+    _check(lib().acs_stencil_plain(u.data_ptr(), a.data_ptr(), out.data_ptr(), ctypes.byref(g), _coef(c),
+                                   _stream_ptr(stream)), "acs_stencil_plain")
+
+
+def acs_stencil_saturated(u, a, out, c=None, halo: int = 4, tile=None, stream=None) -> None:
+    g = grid_for(u, out, halo, 1)
+    if tuple(a.stride()) != tuple(u.stride()) or tuple(a.shape) != tuple(u.shape):
+        raise ValueError("u and a must have the same shape and strides")
+    _check(lib().acs_stencil_saturated(u.data_ptr(), a.data_ptr(), out.data_ptr(), ctypes.byref(g), _coef(c),
+                                       _tile(tile), _stream_ptr(stream)), "acs_stencil_saturated")
+
+
+def acs_status_string(status: int) -> str:
+    return lib().acs_status_string(int(status)).decode()
+
+
+def acs_abi_version() -> int:
+    return int(lib().acs_abi_version())

@@ -1,0 +1,254 @@
+// C-ABI entry points: host-side argument checks, constant folding, dispatch.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <set>
+#include <utility>
+
+#include "acs_internal.cuh"
+
+namespace acs {
+
+static thread_local char t_err[512];
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(t_err, sizeof(t_err), fmt, ap);
+    va_end(ap);
+}
+
+acs_status fail(acs_status s, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(t_err, sizeof(t_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+acs_status launch_status(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ACS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    return ACS_OK;
+}
+
+static std::mutex g_attr_mu;
+static std::set<std::pair<const void*, int>> g_attr_done;
+
+acs_status ensure_smem(const void* fn, size_t bytes) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return launch_status("cudaGetDevice");
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    if (g_attr_done.count({fn, dev})) return ACS_OK;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+        return launch_status("cudaFuncSetAttribute");
+    g_attr_done.insert({fn, dev});
+    return ACS_OK;
+}
+
+int num_sms() {
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (cached[dev] == 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+        cached[dev] = n;
+    }
+    return cached[dev];
+}
+
+// z-chunk per block: balance whole waves of blocks against the per-chunk warm-up (one
+// extra plane of fluxes and the prologue loads, counted as ~1.5 planes of work).
+int default_kchunk(int nz, i64 columns, int ctas_per_sm) {
+    const double slots = (double)num_sms() * (ctas_per_sm > 0 ? ctas_per_sm : 1);
+    static const int cand[] = {4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128};
+    int best = nz;
+    double best_cost = 1e300;
+    for (int kc : cand) {
+        if (kc > nz && kc != cand[0]) break;
+        const i64 chunks = (nz + kc - 1) / kc;
+        const double waves = std::ceil((double)(columns * chunks) / slots);
+        const double cost = waves * ((kc < nz ? kc : nz) + 1.5);
+        if (cost < best_cost - 1e-9) {
+            best_cost = cost;
+            best = kc < nz ? kc : nz;
+        }
+    }
+    return best < 1 ? 1 : best;
+}
+
+}  // namespace acs
+
+using namespace acs;
+
+namespace {
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+// Byte range [lo, hi) touched by an array with the given extents and strides.
+struct Span {
+    uintptr_t lo, hi;
+};
+Span span_of(const double* p, int ncomp, i64 sc, int Z, i64 sz, int Y, i64 sy, int X) {
+    const i64 last = (i64)(ncomp - 1) * sc + (i64)(Z - 1) * sz + (i64)(Y - 1) * sy + (X - 1);
+    return Span{(uintptr_t)p, (uintptr_t)(p + last + 1)};
+}
+bool overlap(Span a, Span b) { return a.lo < b.hi && b.lo < a.hi; }
+
+acs_status check_grid(const acs_grid* g, int radius, int ncomp, Geom& out) {
+    if (!g) return fail(ACS_ERR_INVALID, "grid is NULL");
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1)
+        return fail(ACS_ERR_INVALID, "interior sizes must be >= 1 (got %d x %d x %d)", g->nx, g->ny, g->nz);
+    if (g->nx > (1 << 28) || g->ny > 262140 || g->nz > (1 << 28))
+        return fail(ACS_ERR_INVALID, "interior sizes too large (%d x %d x %d)", g->nx, g->ny, g->nz);
+    if (g->halo < radius) return fail(ACS_ERR_INVALID, "halo %d is smaller than the stencil radius %d", g->halo, radius);
+    if (g->halo > 64) return fail(ACS_ERR_INVALID, "halo %d too large", g->halo);
+    const i64 X = (i64)g->nx + 2 * g->halo, Y = (i64)g->ny + 2 * g->halo, Z = (i64)g->nz + 2 * g->halo;
+    if (g->in_sy < X) return fail(ACS_ERR_INVALID, "in_sy %lld < extended row length %lld", g->in_sy, X);
+    if (g->in_sz < g->in_sy * Y) return fail(ACS_ERR_INVALID, "in_sz %lld < in_sy * extended rows", g->in_sz);
+    if (ncomp > 1 && g->in_sc < g->in_sz * Z) return fail(ACS_ERR_INVALID, "in_sc %lld < in_sz * extended planes", g->in_sc);
+    if (g->out_sy < g->nx) return fail(ACS_ERR_INVALID, "out_sy %lld < nx", g->out_sy);
+    if (g->out_sz < g->out_sy * g->ny) return fail(ACS_ERR_INVALID, "out_sz %lld < out_sy * ny", g->out_sz);
+    if (ncomp > 1 && g->out_sc < g->out_sz * g->nz) return fail(ACS_ERR_INVALID, "out_sc %lld < out_sz * nz", g->out_sc);
+    out.nx = g->nx;
+    out.ny = g->ny;
+    out.nz = g->nz;
+    out.halo = g->halo;
+    out.isy = g->in_sy;
+    out.isz = g->in_sz;
+    out.isc = ncomp > 1 ? g->in_sc : 0;
+    out.osy = g->out_sy;
+    out.osz = g->out_sz;
+    out.osc = ncomp > 1 ? g->out_sc : 0;
+    return ACS_OK;
+}
+
+Span in_span(const double* p, const Geom& g, int ncomp) {
+    return span_of(p, ncomp, g.isc, g.nz + 2 * g.halo, g.isz, g.ny + 2 * g.halo, g.isy, g.nx + 2 * g.halo);
+}
+Span out_span(const double* p, const Geom& g, int ncomp) { return span_of(p, ncomp, g.osc, g.nz, g.osz, g.ny, g.osy, g.nx); }
+
+acs_status check_rhs(const double* U, const double* R, const acs_grid* g, const acs_rhs_params* p, Geom& geo,
+                     RhsConst& k) {
+    if (!U || !R) return fail(ACS_ERR_INVALID, "U or R is NULL");
+    if (!p) return fail(ACS_ERR_INVALID, "params is NULL");
+    if (!aligned(U, 8) || !aligned(R, 8)) return fail(ACS_ERR_ALIGN, "U and R must be 8-byte aligned");
+    acs_status st = check_grid(g, 2, 5, geo);
+    if (st != ACS_OK) return st;
+    if (overlap(in_span(U, geo, 5), out_span(R, geo, 5))) return fail(ACS_ERR_ALIAS, "R overlaps U");
+    for (int d = 0; d < 3; ++d)
+        if (!(std::isfinite(p->h[d]) && p->h[d] != 0.0)) return fail(ACS_ERR_INVALID, "h[%d] must be finite and nonzero", d);
+    if (!std::isfinite(p->gamma) || !std::isfinite(p->eps)) return fail(ACS_ERR_INVALID, "gamma and eps must be finite");
+    k.gamma = p->gamma;
+    k.eps = p->eps;
+    k.g1 = p->gamma - 1.0;
+    k.nhg1 = -0.5 * k.g1;
+    k.sx = -0.5 / p->h[0];
+    k.sy = -0.5 / p->h[1];
+    k.sz = -0.5 / p->h[2];
+    k.hx2i = 0.5 / p->h[0];
+    k.hy2i = 0.5 / p->h[1];
+    k.hz2i = 0.5 / p->h[2];
+    k.neps = -p->eps;
+    return ACS_OK;
+}
+
+acs_status check_star(const double* u, const double* a, const double* out, const acs_grid* g, const double* c,
+                      Geom& geo, StarCoef& cf) {
+    if (!u || !a || !out) return fail(ACS_ERR_INVALID, "u, a or out is NULL");
+    if (!c) return fail(ACS_ERR_INVALID, "coefficients are NULL");
+    if (!aligned(u, 8) || !aligned(a, 8) || !aligned(out, 8)) return fail(ACS_ERR_ALIGN, "arrays must be 8-byte aligned");
+    acs_status st = check_grid(g, 4, 1, geo);
+    if (st != ACS_OK) return st;
+    const Span so = out_span(out, geo, 1);
+    if (overlap(in_span(u, geo, 1), so) || overlap(in_span(a, geo, 1), so)) return fail(ACS_ERR_ALIAS, "out overlaps u or a");
+    double sum = 0.0;
+    for (int q = 0; q < 12; ++q) {
+        if (!std::isfinite(c[q])) return fail(ACS_ERR_INVALID, "coefficient %d is not finite", q);
+        cf.c[q] = c[q];
+    }
+    for (int d = 0; d < 3; ++d)
+        for (int o = 0; o < 4; ++o) sum += c[4 * d + o];
+    cf.c0 = -2.0 * sum;
+    return ACS_OK;
+}
+
+const acs_tile kDefaultRhsTile = {32, 8, 0, 0};
+const acs_tile kDefaultStarTile = {32, 8, 0, 0};
+
+acs_status check_tile(const acs_tile* t, const acs_tile& def, bool (*supported)(int, int), acs_tile& out) {
+    out = t ? *t : def;
+    if (out.flags != 0) return fail(ACS_ERR_INVALID, "tile flags must be 0");
+    if (out.kchunk < 0) return fail(ACS_ERR_INVALID, "kchunk must be >= 0");
+    if (!supported(out.bx, out.by)) return fail(ACS_ERR_UNSUPPORTED, "tile %dx%d is not built", out.bx, out.by);
+    return ACS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+acs_status acs_rhs_plain(const double* U, double* R, const acs_grid* g, const acs_rhs_params* p, acs_stream stream) {
+    Geom geo;
+    RhsConst k;
+    acs_status st = check_rhs(U, R, g, p, geo, k);
+    if (st != ACS_OK) return st;
+    return launch_rhs_plain(U, R, geo, k, (cudaStream_t)stream);
+}
+
+acs_status acs_rhs_saturated(const double* U, double* R, const acs_grid* g, const acs_rhs_params* p,
+                             const acs_tile* tile, acs_stream stream) {
+    Geom geo;
+    RhsConst k;
+    acs_status st = check_rhs(U, R, g, p, geo, k);
+    if (st != ACS_OK) return st;
+    acs_tile t;
+    st = check_tile(tile, kDefaultRhsTile, rhs_tile_supported, t);
+    if (st != ACS_OK) return st;
+    return launch_rhs_saturated(U, R, geo, k, t, (cudaStream_t)stream);
+}
+
+acs_status acs_stencil_plain(const double* u, const double* a, double* out, const acs_grid* g, const double* c,
+                             acs_stream stream) {
+    Geom geo;
+    StarCoef cf;
+    acs_status st = check_star(u, a, out, g, c, geo, cf);
+    if (st != ACS_OK) return st;
+    return launch_stencil_plain(u, a, out, geo, cf, (cudaStream_t)stream);
+}
+
+acs_status acs_stencil_saturated(const double* u, const double* a, double* out, const acs_grid* g, const double* c,
+                                 const acs_tile* tile, acs_stream stream) {
+    Geom geo;
+    StarCoef cf;
+    acs_status st = check_star(u, a, out, g, c, geo, cf);
+    if (st != ACS_OK) return st;
+    acs_tile t;
+    st = check_tile(tile, kDefaultStarTile, star_tile_supported, t);
+    if (st != ACS_OK) return st;
+    return launch_stencil_saturated(u, a, out, geo, cf, t, (cudaStream_t)stream);
+}
+
+const char* acs_status_string(acs_status s) {
+    switch (s) {
+        case ACS_OK: return "ok";
+        case ACS_ERR_INVALID: return "invalid argument";
+        case ACS_ERR_ALIGN: return "misaligned pointer or stride";
+        case ACS_ERR_CUDA: return "CUDA error";
+        case ACS_ERR_UNSUPPORTED: return "unsupported configuration";
+        case ACS_ERR_TIMEOUT: return "device-side wait timed out";
+        case ACS_ERR_NOMODEL: return "no ranker model";
+        case ACS_ERR_ALIAS: return "output overlaps an input";
+        case ACS_ERR_WORKSPACE: return "workspace missing or too small";
+    }
+    return "unknown status";
+}
+
+const char* acs_last_error(void) { return t_err; }
+
+int acs_abi_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,167 @@
+// Variable-coefficient 25-point (radius 4) star stencil, as-written and saturated.
+//
+//   out(p) = sum_{d=x,y,z} sum_{o=1..4} c[d][o-1] * a(p) * (u(p+o e_d) - 2u(p) + u(p-o e_d))
+//
+// As-written: one thread per point, the twelve terms in statement order, each reloading
+// a(p) and u(p) and multiplying by a(p) separately.
+//
+// Saturated (Table I rules plus bulk load, Sec. VI-B):
+//   out(p) = a(p) * (C0 u(p) + sum_d sum_o c[d][o] (u(p+o e_d) + u(p-o e_d))),
+//   C0 = -2 sum c  (folded on the host: constant folding),
+// i.e. the common factor a(p) is pulled out of the twelve terms (distributivity expressed
+// through ASSOC/COMM and FMA1), the twelve copies of -2u(p) merge into one term, and each
+// pair of symmetric neighbours is summed before its single FMA. The xy-planes of u with a
+// 4-cell halo live in a ten-slot shared-memory ring: the nine planes k-4..k+4 in use plus
+// the plane being prefetched with cp.async for the next step.
+#include "acs_internal.cuh"
+
+namespace acs {
+namespace {
+
+__global__ void __launch_bounds__(256) star_plain_kernel(const double* u, const double* a, double* out, Geom g,
+                                                         StarCoef cf) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= g.nx || j >= g.ny) return;
+    const i64 stride[3] = {1, g.isy, g.isz};
+    for (int kk = blockIdx.z; kk < g.nz; kk += gridDim.z) {
+        const i64 p = (i64)(kk + g.halo) * g.isz + (i64)(j + g.halo) * g.isy + (i64)(i + g.halo);
+        double acc = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+#pragma unroll
+            for (int o = 1; o <= 4; ++o) {
+                const i64 s = o * stride[d];
+                acc = acc + cf.c[4 * d + (o - 1)] * a[p] * (u[p + s] - 2.0 * u[p] + u[p - s]);
+            }
+        }
+        out[(i64)kk * g.osz + (i64)j * g.osy + i] = acc;
+    }
+}
+
+template <int BX, int BY>
+struct StarShape {
+    static constexpr int PX = BX + 8, PY = BY + 8, PLANE = PX * PY;
+    static constexpr int NSLOT = 10;
+    static constexpr size_t BYTES = sizeof(double) * (size_t)NSLOT * PLANE;
+    static constexpr int NT = BX * BY;
+};
+
+template <int BX, int BY>
+__device__ __forceinline__ void load_star_plane(double* slot, const double* __restrict__ u, const Geom& g, int i0,
+                                                int j0, int q, int tid) {
+    using S = StarShape<BX, BY>;
+    const int xlim = min(S::PX, g.nx + 8 - i0);
+    const int ylim = min(S::PY, g.ny + 8 - j0);
+    const double* base = u + (i64)(q + g.halo) * g.isz + (i64)(j0 - 4 + g.halo) * g.isy + (i0 - 4 + g.halo);
+#pragma unroll 1
+    for (int e = tid; e < S::PLANE; e += S::NT) {
+        const int yy = e / S::PX;
+        const int xx = e - yy * S::PX;
+        if (xx < xlim && yy < ylim) cp_async8(slot + e, base + (i64)yy * g.isy + xx);
+    }
+}
+
+template <int BX, int BY>
+__global__ void __launch_bounds__(BX * BY) star_saturated_kernel(const double* __restrict__ u,
+                                                                 const double* __restrict__ a,
+                                                                 double* __restrict__ out, Geom g, StarCoef cf,
+                                                                 int kchunk) {
+    using S = StarShape<BX, BY>;
+    constexpr int PX = S::PX, PLANE = S::PLANE;
+    extern __shared__ __align__(16) double smem[];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+    const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
+    const int k0 = blockIdx.z * kchunk;
+    const int k1 = min(k0 + kchunk, g.nz);
+    const int i = i0 + tx, j = j0 + ty;
+    const bool active = (i < g.nx) && (j < g.ny);
+    const int own = (ty + 4) * PX + (tx + 4);
+    auto slot = [&](int q) -> double* { return smem + ((q + S::NSLOT) % S::NSLOT) * PLANE; };
+
+    for (int q = k0 - 4; q <= k0 + 4; ++q) load_star_plane<BX, BY>(slot(q), u, g, i0, j0, q, tid);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+
+    const double* ap = a + (i64)(k0 + g.halo) * g.isz + (i64)(j + g.halo) * g.isy + (i + g.halo);
+    for (int kk = k0; kk < k1; ++kk) {
+        // Bulk-load the plane the next step needs into the slot of plane kk-5.
+        if (kk + 5 <= k1 + 3) load_star_plane<BX, BY>(slot(kk + 5), u, g, i0, j0, kk + 5, tid);
+        cp_async_commit();
+        if (active) {
+            const double av = __ldg(ap);
+            const double* s0 = slot(kk);
+            double t = cf.c0 * s0[own];
+#pragma unroll
+            for (int o = 1; o <= 4; ++o) t = fma(cf.c[o - 1], s0[own + o] + s0[own - o], t);
+#pragma unroll
+            for (int o = 1; o <= 4; ++o) t = fma(cf.c[4 + o - 1], s0[own + o * PX] + s0[own - o * PX], t);
+#pragma unroll
+            for (int o = 1; o <= 4; ++o) t = fma(cf.c[8 + o - 1], slot(kk + o)[own] + slot(kk - o)[own], t);
+            out[(i64)kk * g.osz + (i64)j * g.osy + i] = av * t;
+        }
+        ap += g.isz;
+        cp_async_wait_all();
+        __syncthreads();
+    }
+}
+
+template <int BX, int BY>
+acs_status launch_star_t(const double* u, const double* a, double* out, const Geom& g, const StarCoef& c, int kchunk,
+                         cudaStream_t s) {
+    using S = StarShape<BX, BY>;
+    const void* fn = (const void*)star_saturated_kernel<BX, BY>;
+    acs_status st = ensure_smem(fn, S::BYTES);
+    if (st != ACS_OK) return st;
+    if (kchunk <= 0) {
+        const i64 cols = (i64)((g.nx + BX - 1) / BX) * ((g.ny + BY - 1) / BY);
+        int per_sm = (int)((227u * 1024u) / (S::BYTES + 1024));
+        const int by_threads = 2048 / S::NT;
+        if (per_sm > by_threads) per_sm = by_threads;
+        if (per_sm < 1) per_sm = 1;
+        kchunk = default_kchunk(g.nz, cols, per_sm);
+    }
+    dim3 block(BX, BY, 1);
+    dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, (g.nz + kchunk - 1) / kchunk);
+    star_saturated_kernel<BX, BY><<<grid, block, S::BYTES, s>>>(u, a, out, g, c, kchunk);
+    return launch_status("star_saturated_kernel");
+}
+
+}  // namespace
+
+bool star_tile_supported(int bx, int by) {
+    return (bx == 32 && (by == 4 || by == 8 || by == 16)) || (bx == 64 && (by == 4 || by == 8)) ||
+           (bx == 16 && by == 16);
+}
+
+size_t star_smem_bytes(int bx, int by) {
+    if (bx == 32 && by == 4) return StarShape<32, 4>::BYTES;
+    if (bx == 32 && by == 8) return StarShape<32, 8>::BYTES;
+    if (bx == 32 && by == 16) return StarShape<32, 16>::BYTES;
+    if (bx == 64 && by == 4) return StarShape<64, 4>::BYTES;
+    if (bx == 64 && by == 8) return StarShape<64, 8>::BYTES;
+    if (bx == 16 && by == 16) return StarShape<16, 16>::BYTES;
+    return 0;
+}
+
+acs_status launch_stencil_plain(const double* u, const double* a, double* out, const Geom& g, const StarCoef& c,
+                                cudaStream_t s) {
+    dim3 block(32, 8, 1);
+    dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz < 65535 ? g.nz : 65535);
+    star_plain_kernel<<<grid, block, 0, s>>>(u, a, out, g, c);
+    return launch_status("star_plain_kernel");
+}
+
+acs_status launch_stencil_saturated(const double* u, const double* a, double* out, const Geom& g, const StarCoef& c,
+                                    const acs_tile& t, cudaStream_t s) {
+    if (t.bx == 32 && t.by == 8) return launch_star_t<32, 8>(u, a, out, g, c, t.kchunk, s);
+    if (t.bx == 32 && t.by == 4) return launch_star_t<32, 4>(u, a, out, g, c, t.kchunk, s);
+    if (t.bx == 32 && t.by == 16) return launch_star_t<32, 16>(u, a, out, g, c, t.kchunk, s);
+    if (t.bx == 64 && t.by == 4) return launch_star_t<64, 4>(u, a, out, g, c, t.kchunk, s);
+    if (t.bx == 64 && t.by == 8) return launch_star_t<64, 8>(u, a, out, g, c, t.kchunk, s);
+    if (t.bx == 16 && t.by == 16) return launch_star_t<16, 16>(u, a, out, g, c, t.kchunk, s);
+    return fail(ACS_ERR_UNSUPPORTED, "stencil tile %dx%d is not built", t.bx, t.by);
+}
+
+}  // namespace acs

@@ -1,0 +1,110 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol declared in
+include/acs.h, and rejects bad arguments on the host before any launch.
+
+The pointer values passed here are never dereferenced: argument checks return first.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2306_13002_gb300 import binding
+from paper_2306_13002_gb300 import build as acs_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    acs_build.build()
+    return binding.lib()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "acs.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(acs_\w+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "acs_rhs_saturated" in names and "acs_stencil_plain" in names
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in acs.h but not exported"
+
+
+def test_abi_version_and_status_strings(lib):
+    assert binding.acs_abi_version() >= 100
+    for s in range(9):
+        assert binding.acs_status_string(s) and binding.acs_status_string(s) != "unknown status"
+    assert binding.acs_status_string(99) == "unknown status"
+
+
+FAKE_U = 0x10000000            # 16-byte aligned fake device addresses, never dereferenced
+FAKE_R = 0x40000000
+
+
+def _grid(nx=8, ny=8, nz=8, halo=2, comp=True, pad=0):
+    X, Y, Z = nx + 2 * halo + pad, ny + 2 * halo, nz + 2 * halo
+    return binding.Grid(nx, ny, nz, halo, X, X * Y, X * Y * Z if comp else 0, nx, nx * ny, nx * ny * nz if comp else 0)
+
+
+def _params(h=(1.0, 1.0, 1.0)):
+    return binding.RhsParams(1.4, 0.25, (ctypes.c_double * 3)(*h))
+
+
+def _call_rhs(lib, U, R, g, p, sat=False, tile=None):
+    if sat:
+        t = ctypes.byref(binding.Tile(*tile)) if tile else None
+        return lib.acs_rhs_saturated(U, R, ctypes.byref(g) if g else None, ctypes.byref(p) if p else None, t, None)
+    return lib.acs_rhs_plain(U, R, ctypes.byref(g) if g else None, ctypes.byref(p) if p else None, None)
+
+
+@pytest.mark.parametrize("sat", [False, True])
+def test_rhs_rejects_bad_arguments(lib, sat):
+    E = binding
+    cases = [
+        (None, FAKE_R, _grid(), _params(), 1),
+        (FAKE_U, None, _grid(), _params(), 1),
+        (FAKE_U, FAKE_R, None, _params(), 1),
+        (FAKE_U, FAKE_R, _grid(), None, 1),
+        (FAKE_U + 4, FAKE_R, _grid(), _params(), 2),
+        (FAKE_U, FAKE_R, _grid(nx=0), _params(), 1),
+        (FAKE_U, FAKE_R, _grid(halo=1), _params(), 1),
+        (FAKE_U, FAKE_R, _grid(), _params(h=(1.0, 0.0, 1.0)), 1),
+        (FAKE_U, FAKE_R, _grid(), _params(h=(1.0, float("inf"), 1.0)), 1),
+        (FAKE_U, FAKE_U + 8 * 100, _grid(), _params(), 7),           # output inside the input
+    ]
+    for U, R, g, p, want in cases:
+        st = _call_rhs(lib, U, R, g, p, sat=sat)
+        assert st == want, (st, want, E.acs_status_string(st))
+        assert binding.lib().acs_last_error().decode()
+
+
+def test_rhs_rejects_short_strides(lib):
+    g = _grid()
+    g.in_sy = 8                 # shorter than the extended row (12)
+    assert _call_rhs(lib, FAKE_U, FAKE_R, g, _params()) == 1
+    g = _grid()
+    g.out_sc = 10
+    assert _call_rhs(lib, FAKE_U, FAKE_R, g, _params()) == 1
+
+
+def test_saturated_rejects_unbuilt_tile_and_flags(lib):
+    assert _call_rhs(lib, FAKE_U, FAKE_R, _grid(), _params(), sat=True, tile=(24, 8, 0, 0)) == 4
+    assert _call_rhs(lib, FAKE_U, FAKE_R, _grid(), _params(), sat=True, tile=(32, 8, 0, 1)) == 1
+    assert _call_rhs(lib, FAKE_U, FAKE_R, _grid(), _params(), sat=True, tile=(32, 8, -1, 0)) == 1
+
+
+def test_stencil_rejects_bad_arguments(lib):
+    c = (ctypes.c_double * 12)(*([1.0] * 12))
+    g = _grid(halo=4, comp=False)
+    A = FAKE_U + 0x1000000
+    assert lib.acs_stencil_plain(FAKE_U, A, FAKE_R, ctypes.byref(g), None, None) == 1
+    assert lib.acs_stencil_plain(FAKE_U, A, FAKE_R, ctypes.byref(_grid(halo=3, comp=False)), c, None) == 1
+    assert lib.acs_stencil_plain(FAKE_U, A, A + 80, ctypes.byref(g), c, None) == 7      # out inside a
+    bad = (ctypes.c_double * 12)(*([1.0] * 11 + [float("nan")]))
+    assert lib.acs_stencil_saturated(FAKE_U, A, FAKE_R, ctypes.byref(g), bad, None, None) == 1
+    t = binding.Tile(48, 8, 0, 0)
+    assert lib.acs_stencil_saturated(FAKE_U, A, FAKE_R, ctypes.byref(g), c, ctypes.byref(t), None) == 4

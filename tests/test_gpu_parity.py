@@ -1,0 +1,207 @@
+"""GPU parity: both CUDA forms of both loop bodies, through the C-ABI, against the oracle.
+
+Acceptance per point: |gpu - ref| <= 1e-12 |ref| + 1e-14 (FP64, both forms).
+Small grids are compared in full (several tiles, ragged tails, odd strides); the
+benchmark workloads (RHS 256^3, star stencil 384^3, default launch shape) are compared
+on sampled z-planes that include block-chunk boundaries and the first/last planes.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2306_13002_gb300 import binding, inputs
+from _parity import assert_parity, padded_dev, to_dev
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _rhs_gpu(form, U_np, halo=2, tile=None, h=(1.0, 1.0, 1.0), gamma=1.4, eps=0.25, U_dev=None, R_dev=None):
+    U = to_dev(U_np) if U_dev is None else U_dev
+    nz, ny, nx = (s - 2 * halo for s in U_np.shape[1:])
+    R = torch.full((5, nz, ny, nx), float("nan"), dtype=torch.float64, device="cuda") if R_dev is None else R_dev
+    if form == "plain":
+        binding.acs_rhs_plain(U, R, gamma, eps, h, halo)
+    else:
+        binding.acs_rhs_saturated(U, R, gamma, eps, h, halo, tile=tile)
+    torch.cuda.synchronize()
+    return R
+
+
+def _star_gpu(form, u_np, a_np, c=None, halo=4, tile=None):
+    u, a = to_dev(u_np), to_dev(a_np)
+    nz, ny, nx = (s - 2 * halo for s in u_np.shape)
+    out = torch.full((nz, ny, nx), float("nan"), dtype=torch.float64, device="cuda")
+    if form == "plain":
+        binding.acs_stencil_plain(u, a, out, c, halo)
+    else:
+        binding.acs_stencil_saturated(u, a, out, c, halo, tile=tile)
+    torch.cuda.synchronize()
+    return out
+
+
+# ------------------------------------------------------------------------------- RHS
+
+@pytest.mark.parametrize("form", ["plain", "saturated"])
+def test_rhs_32cubed_full(form):
+    """The 32^3 (+2 halo) workload in full, default launch shape."""
+    U = inputs.rhs_field(32, halo=2, seed=inputs.SEED_RHS_SMALL)
+    ref = oracle.rhs(U, threads=4)
+    R = _rhs_gpu(form, U).cpu().numpy()
+    assert_parity(R, ref, what=f"rhs {form} 32^3")
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (3, 5, 2), (37, 29, 23), (33, 9, 17), (64, 8, 5), (70, 21, 40)])
+@pytest.mark.parametrize("tile", [None, (16, 8, 3), (32, 4, 1), (64, 4, 7), (32, 16, 0), (16, 16, 2)])
+def test_rhs_saturated_ragged(dims, tile):
+    nx, ny, nz = dims
+    U = inputs.rhs_field(nx, ny, nz, halo=2, seed=1000 + nx * 7 + ny * 3 + nz)
+    ref = oracle.rhs(U)
+    R = _rhs_gpu("saturated", U, tile=tile).cpu().numpy()
+    assert_parity(R, ref, what=f"rhs saturated {dims} tile {tile}")
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (37, 29, 23), (70, 21, 40)])
+def test_rhs_plain_ragged(dims):
+    nx, ny, nz = dims
+    U = inputs.rhs_field(nx, ny, nz, halo=2, seed=2000 + nx)
+    ref = oracle.rhs(U)
+    assert_parity(_rhs_gpu("plain", U).cpu().numpy(), ref, what=f"rhs plain {dims}")
+
+
+@pytest.mark.parametrize("form", ["plain", "saturated"])
+def test_rhs_parameters_halo_and_strides(form):
+    """Non-unit spacing per axis, other gamma/eps, a halo of 3, padded input rows and an
+    output written into the interior of a larger NaN-filled buffer (nothing else touched)."""
+    nx, ny, nz, halo = 21, 18, 13, 3
+    U = inputs.rhs_field(nx, ny, nz, halo=halo, seed=3001)
+    h, gamma, eps = (0.75, 1.25, 0.5), 1.67, 0.1
+    ref = oracle.rhs(U, gamma=gamma, eps=eps, h=h, halo=halo)
+    Ud = padded_dev(U, U.shape[-1] + 5)
+    big = torch.full((5, nz + 2, ny + 3, nx + 6), float("nan"), dtype=torch.float64, device="cuda")
+    Rd = big[:, 1:1 + nz, 2:2 + ny, 3:3 + nx]
+    _rhs_gpu(form, U, halo=halo, h=h, gamma=gamma, eps=eps, U_dev=Ud, R_dev=Rd)
+    assert_parity(Rd.cpu().numpy(), ref, what=f"rhs {form} strided")
+    mask = torch.ones_like(big, dtype=torch.bool)
+    mask[:, 1:1 + nz, 2:2 + ny, 3:3 + nx] = False
+    assert torch.isnan(big[mask]).all(), "wrote outside the interior"
+
+
+@pytest.mark.parametrize("form", ["plain", "saturated"])
+@pytest.mark.parametrize("scale_exp", [-500, 500])
+def test_rhs_scaled_fields(form, scale_exp):
+    """U scaled by 2^s scales R by exactly 2^s (every operation scales by a power of two)."""
+    U = inputs.rhs_field(19, 11, 9, halo=2, seed=3100) * (2.0 ** scale_exp)
+    ref = oracle.rhs(U)
+    R = _rhs_gpu(form, U).cpu().numpy()
+    s = 2.0 ** -scale_exp
+    assert_parity(R * s, ref * s, what=f"rhs {form} scaled 2^{scale_exp}")
+
+
+@pytest.mark.parametrize("rho_exp", [-1010, -990, 990, 1010])
+def test_rhs_saturated_reciprocal_range(rho_exp):
+    """rho = 2^e * base, m = 2^(e/2) * base (so |m|^2/rho stays O(1)): at |e| = 1010 the
+    saturated reciprocal takes its IEEE-division fallback, at |e| = 990 the refined
+    estimate. Components have very different scales here, so each is compared relative to
+    its own largest magnitude."""
+    U = inputs.rhs_field(13, 10, 9, halo=2, seed=3200)
+    U[0] *= 2.0 ** rho_exp
+    U[1:4] *= 2.0 ** (rho_exp // 2)
+    ref = oracle.rhs(U)
+    R = _rhs_gpu("saturated", U).cpu().numpy()
+    assert np.isfinite(ref).all()
+    for c in range(5):
+        scale = np.max(np.abs(ref[c]))
+        assert_parity(R[c] / scale, ref[c] / scale, what=f"rhs saturated rho 2^{rho_exp} comp {c}")
+
+
+def test_rhs_constant_dyadic_field_is_zero():
+    """Saturated: each flux value is computed once and differenced against the identical
+    value, so a constant field gives exactly 0. As-written: the compiler contracts the
+    difference of two separately computed fluxes into an FMA, so only the tolerance holds."""
+    U = np.empty((5, 14, 13, 12))
+    for c, v in enumerate((1.25, 0.5, -0.25, 0.125, 2.5)):
+        U[c] = v
+    R = _rhs_gpu("saturated", U).cpu().numpy()
+    assert np.all(R == 0.0)
+    R = _rhs_gpu("plain", U).cpu().numpy()
+    assert np.max(np.abs(R)) <= 1e-14
+
+
+@pytest.mark.parametrize("form", ["plain", "saturated"])
+def test_rhs_128cubed_full(form):
+    U = inputs.rhs_field(128, halo=2, seed=inputs.SEED_RHS_LARGE)
+    ref = oracle.rhs(U, threads=8)
+    assert_parity(_rhs_gpu(form, U).cpu().numpy(), ref, what=f"rhs {form} 128^3")
+
+
+@pytest.mark.parametrize("form", ["plain", "saturated"])
+def test_rhs_256cubed_sampled_planes(form):
+    """The benchmark workload (256^3, default launch) on sampled z-planes."""
+    n = 256
+    U = inputs.rhs_field(n, halo=2, seed=inputs.SEED_RHS_LARGE)
+    R = _rhs_gpu(form, U)
+    planes = [0, 1, 2, 15, 16, 17, 31, 32, 127, 128, 200, 253, 254, 255]
+    for k in planes:
+        ref = oracle.rhs(U, k_range=(k, k + 1), threads=8)[:, k]
+        assert_parity(R[:, k].cpu().numpy(), ref, what=f"rhs {form} 256^3 plane {k}")
+    assert torch.isfinite(R).all()
+
+
+# --------------------------------------------------------------------------- stencil
+
+@pytest.mark.parametrize("form", ["plain", "saturated"])
+def test_stencil_48cubed_full(form):
+    u, a = inputs.stencil_fields(48, seed=inputs.SEED_STENCIL)
+    ref = oracle.stencil(u, a, threads=4)
+    assert_parity(_star_gpu(form, u, a).cpu().numpy(), ref, what=f"stencil {form} 48^3")
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (5, 3, 2), (37, 29, 23), (65, 9, 17), (100, 33, 12)])
+@pytest.mark.parametrize("tile", [None, (32, 4, 3), (64, 8, 0), (16, 16, 5), (64, 4, 1), (32, 16, 2)])
+def test_stencil_saturated_ragged(dims, tile):
+    nx, ny, nz = dims
+    u, a = inputs.stencil_fields(nx, ny, nz, seed=4000 + nx + 5 * ny + 11 * nz)
+    ref = oracle.stencil(u, a)
+    assert_parity(_star_gpu("saturated", u, a, tile=tile).cpu().numpy(), ref, what=f"stencil {dims} {tile}")
+
+
+@pytest.mark.parametrize("form", ["plain", "saturated"])
+def test_stencil_general_coefficients_and_halo(form):
+    """Distinct weights per axis and offset, halo 5."""
+    rng = np.random.default_rng(5)
+    c = rng.uniform(-2, 2, (3, 4))
+    u, a = inputs.stencil_fields(23, 17, 11, halo=5, seed=4100)
+    ref = oracle.stencil(u, a, c, halo=5)
+    assert_parity(_star_gpu(form, u, a, c=c, halo=5).cpu().numpy(), ref, what=f"stencil {form} general c")
+
+
+@pytest.mark.parametrize("form", ["plain", "saturated"])
+def test_stencil_384cubed_sampled_planes(form):
+    n = 384
+    u, a = inputs.stencil_fields(n, seed=inputs.SEED_STENCIL)
+    out = _star_gpu(form, u, a)
+    for k in [0, 3, 4, 7, 8, 63, 64, 191, 192, 380, 383]:
+        ref = oracle.stencil(u, a, k_range=(k, k + 1), threads=8)[k]
+        assert_parity(out[k].cpu().numpy(), ref, what=f"stencil {form} 384^3 plane {k}")
+    assert torch.isfinite(out).all()
+
+
+def test_stencil_constant_field_zero_within_floor():
+    u = np.full((20, 19, 18), 0.7384615)
+    a = inputs.stencil_fields(10, 11, 12, seed=9)[1]
+    for form in ("plain", "saturated"):
+        out = _star_gpu(form, u, a).cpu().numpy()
+        assert np.max(np.abs(out)) <= 1e-14, form
+
+
+# ------------------------------------------------------------------------ error paths
+
+def test_gpu_call_reports_invalid_tile():
+    U = to_dev(inputs.rhs_field(8, halo=2, seed=1))
+    R = torch.zeros((5, 8, 8, 8), dtype=torch.float64, device="cuda")
+    with pytest.raises(binding.AcsError) as ei:
+        binding.acs_rhs_saturated(U, R, tile=(24, 8, 0))
+    assert ei.value.name == "ACS_ERR_UNSUPPORTED"
+    assert torch.all(R == 0)
