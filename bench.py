@@ -56,7 +56,7 @@ NCU_TRAFFIC = {
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("rhs_saturated.cu", "acs_internal.cuh"):
+    for f in ("march.cuh", "rhs_saturated.cu", "acs_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2306_13002_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -195,6 +195,50 @@ def time_launches(torch, fn, steps: int, stream) -> tuple[float, float]:
     return sum(per) / len(per), r0.elapsed_time(r1)
 
 
+def bench_batch(torch, binding, inputs, stream, steps: int) -> dict:
+    """64 star-stencil grids, sides log-uniform in [16, 160]: per-grid launches vs one
+    persistent batch launch vs the autotuned batch replayed from a CUDA graph."""
+    sides = inputs.batch_sides(64, seed=inputs.SEED_BATCH)
+    grids = []
+    for q, (nx, ny, nz) in enumerate(sides):
+        u, a = inputs.stencil_fields(int(nx), int(ny), int(nz), halo=4, seed=inputs.SEED_BATCH + 100 + q)
+        grids.append((torch.from_numpy(u).cuda(), torch.from_numpy(a).cuda(),
+                      torch.empty((int(nz), int(ny), int(nx)), dtype=torch.float64, device="cuda")))
+    points = int(sum(int(a) * int(b) * int(c) for a, b, c in sides))
+    ws = torch.zeros((binding.acs_batch_workspace_bytes(64) + 15) // 16 * 2, dtype=torch.float64, device="cuda")
+    res = {"grids": 64, "points": points}
+
+    def per_grid():
+        for (u, a, out) in grids:
+            binding.acs_stencil_saturated(u, a, out, stream=stream)
+
+    plan = binding.acs_batch_prepare(binding.KIND_STENCIL, grids, ws, stream=stream)
+    batch = lambda: binding.acs_batch_launch(plan, stream=stream)  # noqa: E731
+    for name, fn in (("per_grid_launches", per_grid), ("batch_launch", batch)):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        _, rm = time_launches(torch, fn, steps, stream)
+        res[name] = {"ms": rm / steps, "gpts": points / (rm / steps * 1e-3) / 1e9}
+    tile, _ = binding.acs_autotune_batch(binding.KIND_STENCIL, grids, ws, stream=stream)
+    plan_t = binding.acs_batch_prepare(binding.KIND_STENCIL, grids, ws, tile=tile, stream=stream)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        binding.acs_batch_launch(plan_t, stream=side)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        binding.acs_batch_launch(plan_t, stream=torch.cuda.current_stream())
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+    _, rm = time_launches(torch, graph.replay, steps, stream)
+    res["graph_autotuned"] = {"ms": rm / steps, "gpts": points / (rm / steps * 1e-3) / 1e9, "tile": list(tile)}
+    return res
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -309,6 +353,25 @@ def main() -> None:
         as_written = {"value": plain_value, "ms_per_step": plain_ms, "launch_ms": plain_launch_ms,
                       "speedup_saturated_over_as_written": plain_ms / ms_per_step}
 
+    # The paper's ablation ladder on the same input (Sec. VII code versions).
+    ladder = None
+    if not args.no_plain:
+        ladder = {}
+        for form in ("cse", "cse_sat", "cse_bulk", "accsat"):
+            fn = lambda f=form: binding.acs_rhs_form(U, R, f, stream=stream)  # noqa: E731
+            for _ in range(2):
+                fn()
+            torch.cuda.synchronize()
+            steps_f = max(3, min(args.steps, 40))
+            barrier()
+            lm, rm = time_launches(torch, fn, steps_f, stream)
+            barrier()
+            ms = max_over_ranks(rm) / steps_f
+            ladder[form] = {"ms": ms, "value": sum_over_ranks(points / (ms * 1e-3) / 1e9)}
+        if as_written:
+            ladder["as_written"] = {"ms": as_written["ms_per_step"], "value": as_written["value"]}
+        ladder["saturated"] = {"ms": ms_per_step, "value": value}
+
     # End to end through the public API: pinned host U -> device, kernel, device R -> host.
     def e2e_step():
         U.copy_(U_pin, non_blocking=True)
@@ -359,6 +422,9 @@ def main() -> None:
         res["saturated"]["fp64_gops"] = DP_OPS_PER_POINT["star_saturated"] * m ** 3 / (res["saturated"]["ms"] * 1e-3) / 1e9
         res["saturated"]["hbm_gbs_algorithmic"] = star_bytes / (res["saturated"]["ms"] * 1e-3) / 1e9
         stencil = {"grid": [m] * 3, "halo": 4, **res}
+        del u, a, out
+        torch.cuda.empty_cache()
+        stencil["batch64"] = bench_batch(torch, binding, inputs, stream, max(3, min(args.steps, 50)))
 
     if rank != 0:
         if dist:
@@ -393,6 +459,7 @@ def main() -> None:
                 "peak_gbs": hbm_peak, "frac": algo_bytes / (launch_ms * 1e-3) / 1e9 / hbm_peak,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6800"},
         "as_written": as_written,
+        "ladder": ladder,
         "kernel_launch_ms": launch_ms,
         "e2e": e2e,
         "gpu_launches": args.steps,

@@ -85,6 +85,27 @@ typedef struct acs_rhs_params {
     double h[3];                       /* grid spacing along x, y, z; each nonzero */
 } acs_rhs_params;
 
+/*
+ * Code versions of the RHS loop body (paper Sec. VII, the four variants compared there,
+ * plus the two ends of the ladder):
+ *   ACS_FORM_AS_WRITTEN  the original body (acs_rhs_plain)
+ *   ACS_FORM_CSE         shared subexpressions counted once (Sec. IV-B), temporaries at
+ *                        first use (Sec. VI-A), no rewriting rules
+ *   ACS_FORM_CSE_SAT     CSE plus the Table I rules (FMA, ASSOC/COMM, constant folding)
+ *   ACS_FORM_CSE_BULK    CSE plus bulk load (Sec. VI-B): all 65 loads before the first store
+ *   ACS_FORM_ACCSAT      CSE + SAT + BULK (the paper's full tool)
+ *   ACS_FORM_SATURATED   the cross-iteration saturated kernel (acs_rhs_saturated)
+ * The four middle forms rewrite each iteration on its own, one thread per point.
+ */
+typedef enum acs_form {
+    ACS_FORM_AS_WRITTEN = 0,
+    ACS_FORM_CSE = 1,
+    ACS_FORM_CSE_SAT = 2,
+    ACS_FORM_CSE_BULK = 3,
+    ACS_FORM_ACCSAT = 4,
+    ACS_FORM_SATURATED = 5
+} acs_form;
+
 /* Launch shape of a saturated kernel. A NULL tile selects the built-in default. */
 typedef struct acs_tile {
     int bx;       /* threads (points) along x per block: 16, 32 or 64 */
@@ -115,6 +136,14 @@ acs_status acs_rhs_saturated(const double *U, double *R, const acs_grid *g, cons
                              const acs_tile *tile, acs_stream stream);
 
 /*
+ * acs_rhs_form - the RHS in one of the acs_form code versions (same arguments as
+ * acs_rhs_saturated; `tile` is used by ACS_FORM_SATURATED only). ACS_ERR_INVALID for an
+ * unknown form.
+ */
+acs_status acs_rhs_form(const double *U, double *R, const acs_grid *g, const acs_rhs_params *p, int form,
+                        const acs_tile *tile, acs_stream stream);
+
+/*
  * acs_stencil_plain - as-written 25-point star stencil, loop body (2).
  *   u, a   inputs with the same geometry, halo >= 4 (only a at interior points is read)
  *   out    output, interior only
@@ -131,6 +160,73 @@ acs_status acs_stencil_plain(const double *u, const double *a, double *out, cons
  */
 acs_status acs_stencil_saturated(const double *u, const double *a, double *out, const acs_grid *g,
                                  const double *c, const acs_tile *tile, acs_stream stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Batched persistent launch (many grids of uneven sizes, one kernel launch).
+ *
+ * Each grid is cut into work units (tile x z-chunk); a persistent grid of blocks pops units
+ * from an atomic counter kept in a caller-provided device workspace, so any number of
+ * grids costs one launch. Use: acs_batch_workspace_bytes(n) -> allocate -> acs_batch_prepare
+ * (validates every item, uploads the unit table, synchronises `stream`) -> acs_batch_launch
+ * as often as needed. acs_batch_launch enqueues a memset of the counter and one kernel on
+ * `stream`; it may be captured in a CUDA graph. The items' buffers and the workspace must
+ * stay valid while launches are in flight; launches sharing one workspace must not overlap.
+ * ------------------------------------------------------------------------------------- */
+typedef enum acs_kind {
+    ACS_KIND_RHS = 0,      /* loop body (1); params: const acs_rhs_params*  */
+    ACS_KIND_STENCIL = 1   /* loop body (2); params: const double[12] weights */
+} acs_kind;
+
+typedef struct acs_batch_item {
+    const double *in0;     /* U (RHS) or u (stencil), device */
+    const double *in1;     /* NULL (RHS) or a (stencil), device */
+    double *out;           /* R (RHS) or out (stencil), device */
+    acs_grid g;            /* this grid's geometry (addressing rules above) */
+} acs_batch_item;
+
+typedef struct acs_batch_plan {      /* filled by acs_batch_prepare; treat as opaque */
+    int kind;
+    int n;
+    acs_tile tile;
+    long long total_units;
+    void *ws;
+    size_t ws_bytes;
+} acs_batch_plan;
+
+/* Device workspace bytes acs_batch_prepare needs for n grids (0 if n < 1). */
+size_t acs_batch_workspace_bytes(int n);
+
+/*
+ * acs_batch_prepare - check n >= 1 items of one kind (each as its single-grid entry point
+ * would, including the alias check), order them largest first, and upload the unit table
+ * into `ws` (16-byte aligned device memory of at least acs_batch_workspace_bytes(n) bytes:
+ * ACS_ERR_ALIGN / ACS_ERR_WORKSPACE otherwise). `tile` NULL = 32 x 8 with z-chunks of 16
+ * planes. On success fills `plan`.
+ */
+acs_status acs_batch_prepare(const acs_batch_item *items, int n, int kind, const acs_tile *tile, void *ws,
+                             size_t ws_bytes, acs_batch_plan *plan, acs_stream stream);
+
+/* acs_batch_launch - run a prepared batch; `params` as given for its kind above. */
+acs_status acs_batch_launch(const acs_batch_plan *plan, const void *params, acs_stream stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Launch-shape autotuner. Each call times every built tile with several z-chunk lengths on
+ * the caller's buffers (outputs are overwritten, `stream` is synchronised: do not capture),
+ * returns the fastest shape in `best` (and its time in `best_ms` if non-NULL) and records it
+ * in a process-wide cache keyed by the workload shape. acs_rhs_saturated and
+ * acs_stencil_saturated called with tile == NULL use the cached shape for their grid size.
+ * ------------------------------------------------------------------------------------- */
+acs_status acs_autotune_rhs(const double *U, double *R, const acs_grid *g, const acs_rhs_params *p,
+                            acs_tile *best, float *best_ms, acs_stream stream);
+acs_status acs_autotune_stencil(const double *u, const double *a, double *out, const acs_grid *g,
+                                const double *c, acs_tile *best, float *best_ms, acs_stream stream);
+acs_status acs_autotune_batch(const acs_batch_item *items, int n, int kind, const void *params, void *ws,
+                              size_t ws_bytes, acs_tile *best, float *best_ms, acs_stream stream);
+/* Save / load (merge) / clear the tuning cache; a small versioned text file. */
+acs_status acs_tune_cache_save(const char *path);
+acs_status acs_tune_cache_load(const char *path);
+void acs_tune_cache_clear(void);
+int acs_tune_cache_size(void);
 
 /* Static text for a status code. */
 const char *acs_status_string(acs_status s);

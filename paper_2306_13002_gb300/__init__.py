@@ -6,5 +6,5 @@ exposes its C-ABI entry points under the same names. `inputs` holds the seeded i
 generators. Importing the package does not load the CUDA library; the first call does,
 and fails loudly if it is missing.
 """
-from .binding import (AcsError, acs_abi_version, acs_rhs_plain, acs_rhs_saturated,  # noqa: F401
+from .binding import (AcsError, acs_abi_version, acs_rhs_form, acs_rhs_plain, acs_rhs_saturated,  # noqa: F401
                       acs_stencil_plain, acs_stencil_saturated, acs_status_string)

@@ -45,11 +45,26 @@ class Tile(ctypes.Structure):
     _fields_ = [("bx", ctypes.c_int), ("by", ctypes.c_int), ("kchunk", ctypes.c_int), ("flags", ctypes.c_int)]
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("in0", ctypes.c_void_p), ("in1", ctypes.c_void_p), ("out", ctypes.c_void_p), ("g", Grid)]
+
+
+class BatchPlan(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("n", ctypes.c_int), ("tile", Tile), ("total_units", ctypes.c_longlong),
+                ("ws", ctypes.c_void_p), ("ws_bytes", ctypes.c_size_t)]
+
+
+KIND_RHS, KIND_STENCIL = 0, 1
+
 _lock = threading.Lock()
 _lib = None
 
-EXPORTS = ("acs_rhs_plain", "acs_rhs_saturated", "acs_stencil_plain", "acs_stencil_saturated",
-           "acs_status_string", "acs_last_error", "acs_abi_version")
+FORMS = {"as_written": 0, "cse": 1, "cse_sat": 2, "cse_bulk": 3, "accsat": 4, "saturated": 5}
+
+EXPORTS = ("acs_rhs_plain", "acs_rhs_saturated", "acs_rhs_form", "acs_stencil_plain", "acs_stencil_saturated",
+           "acs_batch_workspace_bytes", "acs_batch_prepare", "acs_batch_launch", "acs_autotune_rhs",
+           "acs_autotune_stencil", "acs_autotune_batch", "acs_tune_cache_save", "acs_tune_cache_load",
+           "acs_tune_cache_clear", "acs_tune_cache_size", "acs_status_string", "acs_last_error", "acs_abi_version")
 
 
 def lib() -> ctypes.CDLL:
@@ -65,10 +80,30 @@ def lib() -> ctypes.CDLL:
             L.acs_rhs_plain.argtypes = [p, p, ctypes.POINTER(Grid), ctypes.POINTER(RhsParams), p]
             L.acs_rhs_saturated.argtypes = [p, p, ctypes.POINTER(Grid), ctypes.POINTER(RhsParams),
                                             ctypes.POINTER(Tile), p]
+            L.acs_rhs_form.argtypes = [p, p, ctypes.POINTER(Grid), ctypes.POINTER(RhsParams), st,
+                                       ctypes.POINTER(Tile), p]
             L.acs_stencil_plain.argtypes = [p, p, p, ctypes.POINTER(Grid), ctypes.POINTER(ctypes.c_double), p]
             L.acs_stencil_saturated.argtypes = [p, p, p, ctypes.POINTER(Grid), ctypes.POINTER(ctypes.c_double),
                                                 ctypes.POINTER(Tile), p]
-            for f in ("acs_rhs_plain", "acs_rhs_saturated", "acs_stencil_plain", "acs_stencil_saturated"):
+            for f in ("acs_rhs_plain", "acs_rhs_saturated", "acs_rhs_form", "acs_stencil_plain",
+                      "acs_stencil_saturated"):
+                getattr(L, f).restype = st
+            T, G = ctypes.POINTER(Tile), ctypes.POINTER(Grid)
+            f32p = ctypes.POINTER(ctypes.c_float)
+            L.acs_batch_workspace_bytes.argtypes = [st]
+            L.acs_batch_workspace_bytes.restype = ctypes.c_size_t
+            L.acs_batch_prepare.argtypes = [ctypes.POINTER(BatchItem), st, st, T, p, ctypes.c_size_t,
+                                            ctypes.POINTER(BatchPlan), p]
+            L.acs_batch_launch.argtypes = [ctypes.POINTER(BatchPlan), p, p]
+            L.acs_autotune_rhs.argtypes = [p, p, G, ctypes.POINTER(RhsParams), T, f32p, p]
+            L.acs_autotune_stencil.argtypes = [p, p, p, G, ctypes.POINTER(ctypes.c_double), T, f32p, p]
+            L.acs_autotune_batch.argtypes = [ctypes.POINTER(BatchItem), st, st, p, p, ctypes.c_size_t, T, f32p, p]
+            L.acs_tune_cache_save.argtypes = [ctypes.c_char_p]
+            L.acs_tune_cache_load.argtypes = [ctypes.c_char_p]
+            L.acs_tune_cache_clear.restype = None
+            L.acs_tune_cache_size.restype = st
+            for f in ("acs_batch_prepare", "acs_batch_launch", "acs_autotune_rhs", "acs_autotune_stencil",
+                      "acs_autotune_batch", "acs_tune_cache_save", "acs_tune_cache_load"):
                 getattr(L, f).restype = st
             L.acs_status_string.argtypes = [st]
             L.acs_status_string.restype = ctypes.c_char_p
@@ -145,6 +180,16 @@ def acs_rhs_saturated(U, R, gamma: float = 1.4, eps: float = 0.25, h=(1.0, 1.0, 
                                    _stream_ptr(stream)), "acs_rhs_saturated")
 
 
+def acs_rhs_form(U, R, form, gamma: float = 1.4, eps: float = 0.25, h=(1.0, 1.0, 1.0), halo: int = 2,
+                 tile=None, stream=None) -> None:
+    """RHS in one code version; `form` is an acs_form value or a name from FORMS."""
+    f = FORMS[form] if isinstance(form, str) else int(form)
+    g = grid_for(U, R, halo, 5)
+    pr = _params(gamma, eps, h)
+    _check(lib().acs_rhs_form(U.data_ptr(), R.data_ptr(), ctypes.byref(g), ctypes.byref(pr), f, _tile(tile),
+                              _stream_ptr(stream)), "acs_rhs_form")
+
+
 def _coef(c) -> ctypes.Array:
     if c is None:
         vals = list(TAYLOR8) * 3
@@ -177,3 +222,92 @@ def acs_status_string(status: int) -> str:
 
 def acs_abi_version() -> int:
     return int(lib().acs_abi_version())
+
+
+# ------------------------------------------------------------------ batch and autotune
+
+def acs_batch_workspace_bytes(n: int) -> int:
+    return int(lib().acs_batch_workspace_bytes(int(n)))
+
+
+def batch_items(kind: int, grids, halo: int | None = None):
+    """ctypes array of acs_batch_item from (in0, in1, out) tensor triples (in1 None for the RHS)."""
+    halo = (2 if kind == KIND_RHS else 4) if halo is None else halo
+    arr = (BatchItem * len(grids))()
+    for q, (in0, in1, out) in enumerate(grids):
+        g = grid_for(in0, out, halo, 5 if kind == KIND_RHS else 1)
+        arr[q] = BatchItem(in0.data_ptr(), in1.data_ptr() if in1 is not None else None, out.data_ptr(), g)
+    return arr
+
+
+def _batch_params(kind: int, params):
+    """(void* for the C call, object to keep alive during the call)."""
+    if kind == KIND_RHS:
+        if params is None:
+            params = {}
+        pr = params if isinstance(params, RhsParams) else _params(
+            params.get("gamma", 1.4), params.get("eps", 0.25), params.get("h", (1.0, 1.0, 1.0)))
+        return ctypes.cast(ctypes.pointer(pr), ctypes.c_void_p), pr
+    c = _coef(params)
+    return ctypes.cast(c, ctypes.c_void_p), c
+
+
+def acs_batch_prepare(kind: int, grids, ws, tile=None, halo: int | None = None, stream=None) -> BatchPlan:
+    """Validate and upload a batch; `ws` is a device tensor of >= acs_batch_workspace_bytes(n) bytes."""
+    items = batch_items(kind, grids, halo)
+    plan = BatchPlan()
+    nbytes = ws.numel() * ws.element_size()
+    _check(lib().acs_batch_prepare(items, len(grids), kind, _tile(tile), ws.data_ptr(), nbytes, ctypes.byref(plan),
+                                   _stream_ptr(stream)), "acs_batch_prepare")
+    plan._keep = (items, ws, grids)
+    return plan
+
+
+def acs_batch_launch(plan: BatchPlan, params=None, stream=None) -> None:
+    ptr, keep = _batch_params(plan.kind, params)
+    _check(lib().acs_batch_launch(ctypes.byref(plan), ptr, _stream_ptr(stream)), "acs_batch_launch")
+    del keep
+
+
+def acs_autotune_rhs(U, R, gamma=1.4, eps=0.25, h=(1.0, 1.0, 1.0), halo=2, stream=None):
+    g = grid_for(U, R, halo, 5)
+    pr = _params(gamma, eps, h)
+    t, ms = Tile(), ctypes.c_float()
+    _check(lib().acs_autotune_rhs(U.data_ptr(), R.data_ptr(), ctypes.byref(g), ctypes.byref(pr), ctypes.byref(t),
+                                  ctypes.byref(ms), _stream_ptr(stream)), "acs_autotune_rhs")
+    return (t.bx, t.by, t.kchunk), ms.value
+
+
+def acs_autotune_stencil(u, a, out, c=None, halo=4, stream=None):
+    g = grid_for(u, out, halo, 1)
+    t, ms = Tile(), ctypes.c_float()
+    _check(lib().acs_autotune_stencil(u.data_ptr(), a.data_ptr(), out.data_ptr(), ctypes.byref(g), _coef(c),
+                                      ctypes.byref(t), ctypes.byref(ms), _stream_ptr(stream)), "acs_autotune_stencil")
+    return (t.bx, t.by, t.kchunk), ms.value
+
+
+def acs_autotune_batch(kind: int, grids, ws, params=None, halo=None, stream=None):
+    items = batch_items(kind, grids, halo)
+    ptr, keep = _batch_params(kind, params)
+    t, ms = Tile(), ctypes.c_float()
+    nbytes = ws.numel() * ws.element_size()
+    _check(lib().acs_autotune_batch(items, len(grids), kind, ptr, ws.data_ptr(), nbytes, ctypes.byref(t),
+                                    ctypes.byref(ms), _stream_ptr(stream)), "acs_autotune_batch")
+    del keep
+    return (t.bx, t.by, t.kchunk), ms.value
+
+
+def acs_tune_cache_save(path: str) -> None:
+    _check(lib().acs_tune_cache_save(path.encode()), "acs_tune_cache_save")
+
+
+def acs_tune_cache_load(path: str) -> None:
+    _check(lib().acs_tune_cache_load(path.encode()), "acs_tune_cache_load")
+
+
+def acs_tune_cache_clear() -> None:
+    lib().acs_tune_cache_clear()
+
+
+def acs_tune_cache_size() -> int:
+    return int(lib().acs_tune_cache_size())

@@ -6,6 +6,7 @@
 #include <mutex>
 #include <set>
 #include <utility>
+#include <vector>
 
 #include "acs_internal.cuh"
 
@@ -131,6 +132,9 @@ Span in_span(const double* p, const Geom& g, int ncomp) {
 }
 Span out_span(const double* p, const Geom& g, int ncomp) { return span_of(p, ncomp, g.osc, g.nz, g.osz, g.ny, g.osy, g.nx); }
 
+acs_status rhs_const(const acs_rhs_params* p, RhsConst& k);
+acs_status star_coef(const double* c, StarCoef& cf);
+
 acs_status check_rhs(const double* U, const double* R, const acs_grid* g, const acs_rhs_params* p, Geom& geo,
                      RhsConst& k) {
     if (!U || !R) return fail(ACS_ERR_INVALID, "U or R is NULL");
@@ -139,6 +143,11 @@ acs_status check_rhs(const double* U, const double* R, const acs_grid* g, const 
     acs_status st = check_grid(g, 2, 5, geo);
     if (st != ACS_OK) return st;
     if (overlap(in_span(U, geo, 5), out_span(R, geo, 5))) return fail(ACS_ERR_ALIAS, "R overlaps U");
+    return rhs_const(p, k);
+}
+
+acs_status rhs_const(const acs_rhs_params* p, RhsConst& k) {
+    if (!p) return fail(ACS_ERR_INVALID, "params is NULL");
     for (int d = 0; d < 3; ++d)
         if (!(std::isfinite(p->h[d]) && p->h[d] != 0.0)) return fail(ACS_ERR_INVALID, "h[%d] must be finite and nonzero", d);
     if (!std::isfinite(p->gamma) || !std::isfinite(p->eps)) return fail(ACS_ERR_INVALID, "gamma and eps must be finite");
@@ -153,6 +162,7 @@ acs_status check_rhs(const double* U, const double* R, const acs_grid* g, const 
     k.hy2i = 0.5 / p->h[1];
     k.hz2i = 0.5 / p->h[2];
     k.neps = -p->eps;
+    k.pp = Pipe{1.0, -1.0, -0.0};
     return ACS_OK;
 }
 
@@ -165,6 +175,11 @@ acs_status check_star(const double* u, const double* a, const double* out, const
     if (st != ACS_OK) return st;
     const Span so = out_span(out, geo, 1);
     if (overlap(in_span(u, geo, 1), so) || overlap(in_span(a, geo, 1), so)) return fail(ACS_ERR_ALIAS, "out overlaps u or a");
+    return star_coef(c, cf);
+}
+
+acs_status star_coef(const double* c, StarCoef& cf) {
+    if (!c) return fail(ACS_ERR_INVALID, "coefficients are NULL");
     double sum = 0.0;
     for (int q = 0; q < 12; ++q) {
         if (!std::isfinite(c[q])) return fail(ACS_ERR_INVALID, "coefficient %d is not finite", q);
@@ -173,14 +188,55 @@ acs_status check_star(const double* u, const double* a, const double* out, const
     for (int d = 0; d < 3; ++d)
         for (int o = 0; o < 4; ++o) sum += c[4 * d + o];
     cf.c0 = -2.0 * sum;
+    cf.pp = Pipe{1.0, -1.0, -0.0};
     return ACS_OK;
+}
+
+// Every item of a batch is checked as its single-grid entry point would check it.
+acs_status check_batch_items(const acs_batch_item* items, int n, int kind, std::vector<Geom>& geo) {
+    if (!items) return fail(ACS_ERR_INVALID, "items is NULL");
+    if (n < 1 || n > (1 << 20)) return fail(ACS_ERR_INVALID, "batch size %d out of range [1, 2^20]", n);
+    if (kind != ACS_KIND_RHS && kind != ACS_KIND_STENCIL) return fail(ACS_ERR_INVALID, "unknown batch kind %d", kind);
+    geo.resize(n);
+    for (int q = 0; q < n; ++q) {
+        const acs_batch_item& it = items[q];
+        acs_status st;
+        if (kind == ACS_KIND_RHS) {
+            if (!it.in0 || !it.out) return fail(ACS_ERR_INVALID, "item %d: U or R is NULL", q);
+            if (!aligned(it.in0, 8) || !aligned(it.out, 8)) return fail(ACS_ERR_ALIGN, "item %d: misaligned", q);
+            st = check_grid(&it.g, 2, 5, geo[q]);
+            if (st != ACS_OK) return st;
+            if (overlap(in_span(it.in0, geo[q], 5), out_span(it.out, geo[q], 5)))
+                return fail(ACS_ERR_ALIAS, "item %d: R overlaps U", q);
+        } else {
+            if (!it.in0 || !it.in1 || !it.out) return fail(ACS_ERR_INVALID, "item %d: u, a or out is NULL", q);
+            if (!aligned(it.in0, 8) || !aligned(it.in1, 8) || !aligned(it.out, 8))
+                return fail(ACS_ERR_ALIGN, "item %d: misaligned", q);
+            st = check_grid(&it.g, 4, 1, geo[q]);
+            if (st != ACS_OK) return st;
+            const Span so = out_span(it.out, geo[q], 1);
+            if (overlap(in_span(it.in0, geo[q], 1), so) || overlap(in_span(it.in1, geo[q], 1), so))
+                return fail(ACS_ERR_ALIAS, "item %d: out overlaps u or a", q);
+        }
+    }
+    return ACS_OK;
+}
+
+acs_status batch_params(int kind, const void* params, RhsConst& rk, StarCoef& sc) {
+    std::memset(&rk, 0, sizeof(rk));
+    std::memset(&sc, 0, sizeof(sc));
+    if (!params) return fail(ACS_ERR_INVALID, "params is NULL");
+    if (kind == ACS_KIND_RHS) return rhs_const(static_cast<const acs_rhs_params*>(params), rk);
+    return star_coef(static_cast<const double*>(params), sc);
 }
 
 const acs_tile kDefaultRhsTile = {32, 8, 0, 0};
 const acs_tile kDefaultStarTile = {32, 8, 0, 0};
 
-acs_status check_tile(const acs_tile* t, const acs_tile& def, bool (*supported)(int, int), acs_tile& out) {
+acs_status check_tile(const acs_tile* t, const acs_tile& def, bool (*supported)(int, int), acs_tile& out,
+                      int kind = -1, const Geom* g = nullptr) {
     out = t ? *t : def;
+    if (!t && g && tuned_tile(kind, *g, &out)) return ACS_OK;
     if (out.flags != 0) return fail(ACS_ERR_INVALID, "tile flags must be 0");
     if (out.kchunk < 0) return fail(ACS_ERR_INVALID, "kchunk must be >= 0");
     if (!supported(out.bx, out.by)) return fail(ACS_ERR_UNSUPPORTED, "tile %dx%d is not built", out.bx, out.by);
@@ -206,9 +262,21 @@ acs_status acs_rhs_saturated(const double* U, double* R, const acs_grid* g, cons
     acs_status st = check_rhs(U, R, g, p, geo, k);
     if (st != ACS_OK) return st;
     acs_tile t;
-    st = check_tile(tile, kDefaultRhsTile, rhs_tile_supported, t);
+    st = check_tile(tile, kDefaultRhsTile, rhs_tile_supported, t, ACS_KIND_RHS, &geo);
     if (st != ACS_OK) return st;
     return launch_rhs_saturated(U, R, geo, k, t, (cudaStream_t)stream);
+}
+
+acs_status acs_rhs_form(const double* U, double* R, const acs_grid* g, const acs_rhs_params* p, int form,
+                        const acs_tile* tile, acs_stream stream) {
+    if (form == ACS_FORM_AS_WRITTEN) return acs_rhs_plain(U, R, g, p, stream);
+    if (form == ACS_FORM_SATURATED) return acs_rhs_saturated(U, R, g, p, tile, stream);
+    if (form < ACS_FORM_CSE || form > ACS_FORM_ACCSAT) return fail(ACS_ERR_INVALID, "unknown RHS form %d", form);
+    Geom geo;
+    RhsConst k;
+    acs_status st = check_rhs(U, R, g, p, geo, k);
+    if (st != ACS_OK) return st;
+    return launch_rhs_ladder(U, R, geo, k, form, (cudaStream_t)stream);
 }
 
 acs_status acs_stencil_plain(const double* u, const double* a, double* out, const acs_grid* g, const double* c,
@@ -227,10 +295,100 @@ acs_status acs_stencil_saturated(const double* u, const double* a, double* out, 
     acs_status st = check_star(u, a, out, g, c, geo, cf);
     if (st != ACS_OK) return st;
     acs_tile t;
-    st = check_tile(tile, kDefaultStarTile, star_tile_supported, t);
+    st = check_tile(tile, kDefaultStarTile, star_tile_supported, t, ACS_KIND_STENCIL, &geo);
     if (st != ACS_OK) return st;
     return launch_stencil_saturated(u, a, out, geo, cf, t, (cudaStream_t)stream);
 }
+
+size_t acs_batch_workspace_bytes(int n) { return batch_ws_bytes(n); }
+
+acs_status acs_batch_prepare(const acs_batch_item* items, int n, int kind, const acs_tile* tile, void* ws,
+                             size_t ws_bytes, acs_batch_plan* plan, acs_stream stream) {
+    if (!plan) return fail(ACS_ERR_INVALID, "plan is NULL");
+    std::vector<Geom> geo;
+    acs_status st = check_batch_items(items, n, kind, geo);
+    if (st != ACS_OK) return st;
+    if (!ws) return fail(ACS_ERR_WORKSPACE, "workspace is NULL");
+    if (!aligned(ws, 16)) return fail(ACS_ERR_ALIGN, "workspace must be 16-byte aligned");
+    if (ws_bytes < batch_ws_bytes(n))
+        return fail(ACS_ERR_WORKSPACE, "workspace %zu bytes < %zu needed for %d grids", ws_bytes, batch_ws_bytes(n), n);
+    acs_tile t = tile ? *tile : acs_tile{32, 8, 16, 0};
+    if (t.kchunk == 0) t.kchunk = 16;
+    if (t.flags != 0 || t.kchunk < 1) return fail(ACS_ERR_INVALID, "bad batch tile (kchunk %d, flags %d)", t.kchunk, t.flags);
+    if (!(kind == ACS_KIND_RHS ? rhs_tile_supported(t.bx, t.by) : star_tile_supported(t.bx, t.by)))
+        return fail(ACS_ERR_UNSUPPORTED, "tile %dx%d is not built", t.bx, t.by);
+    BatchPlanHost hp;
+    st = batch_prepare_host(items, geo.data(), n, kind, t, (unsigned char*)ws, ws_bytes, (cudaStream_t)stream, hp);
+    if (st != ACS_OK) return st;
+    plan->kind = kind;
+    plan->n = n;
+    plan->tile = t;
+    plan->total_units = hp.total;
+    plan->ws = ws;
+    plan->ws_bytes = ws_bytes;
+    return ACS_OK;
+}
+
+acs_status acs_batch_launch(const acs_batch_plan* plan, const void* params, acs_stream stream) {
+    if (!plan) return fail(ACS_ERR_INVALID, "plan is NULL");
+    if (plan->kind != ACS_KIND_RHS && plan->kind != ACS_KIND_STENCIL) return fail(ACS_ERR_INVALID, "plan kind is invalid");
+    if (!plan->ws || plan->n < 1 || plan->total_units < 1 || plan->ws_bytes < batch_ws_bytes(plan->n))
+        return fail(ACS_ERR_INVALID, "plan was not filled by acs_batch_prepare");
+    RhsConst rk;
+    StarCoef sc;
+    acs_status st = batch_params(plan->kind, params, rk, sc);
+    if (st != ACS_OK) return st;
+    BatchPlanHost hp{(unsigned char*)plan->ws, plan->ws_bytes, plan->kind, plan->n, plan->tile, plan->total_units};
+    return batch_launch(hp, rk, sc, (cudaStream_t)stream);
+}
+
+acs_status acs_autotune_rhs(const double* U, double* R, const acs_grid* g, const acs_rhs_params* p, acs_tile* best,
+                            float* best_ms, acs_stream stream) {
+    Geom geo;
+    RhsConst k;
+    acs_status st = check_rhs(U, R, g, p, geo, k);
+    if (st != ACS_OK) return st;
+    return tune_rhs(U, R, geo, k, (cudaStream_t)stream, best, best_ms);
+}
+
+acs_status acs_autotune_stencil(const double* u, const double* a, double* out, const acs_grid* g, const double* c,
+                                acs_tile* best, float* best_ms, acs_stream stream) {
+    Geom geo;
+    StarCoef cf;
+    acs_status st = check_star(u, a, out, g, c, geo, cf);
+    if (st != ACS_OK) return st;
+    return tune_stencil(u, a, out, geo, cf, (cudaStream_t)stream, best, best_ms);
+}
+
+acs_status acs_autotune_batch(const acs_batch_item* items, int n, int kind, const void* params, void* ws,
+                              size_t ws_bytes, acs_tile* best, float* best_ms, acs_stream stream) {
+    std::vector<Geom> geo;
+    acs_status st = check_batch_items(items, n, kind, geo);
+    if (st != ACS_OK) return st;
+    if (!ws) return fail(ACS_ERR_WORKSPACE, "workspace is NULL");
+    if (!aligned(ws, 16)) return fail(ACS_ERR_ALIGN, "workspace must be 16-byte aligned");
+    if (ws_bytes < batch_ws_bytes(n)) return fail(ACS_ERR_WORKSPACE, "workspace too small");
+    RhsConst rk;
+    StarCoef sc;
+    st = batch_params(kind, params, rk, sc);
+    if (st != ACS_OK) return st;
+    return tune_batch(items, geo.data(), n, kind, rk, sc, (unsigned char*)ws, ws_bytes, (cudaStream_t)stream, best,
+                      best_ms);
+}
+
+acs_status acs_tune_cache_save(const char* path) {
+    if (!path) return fail(ACS_ERR_INVALID, "path is NULL");
+    return tune_cache_save(path);
+}
+
+acs_status acs_tune_cache_load(const char* path) {
+    if (!path) return fail(ACS_ERR_INVALID, "path is NULL");
+    return tune_cache_load(path);
+}
+
+void acs_tune_cache_clear(void) { tune_cache_clear(); }
+
+int acs_tune_cache_size(void) { return tune_cache_size(); }
 
 const char* acs_status_string(acs_status s) {
     switch (s) {

@@ -17,6 +17,20 @@ struct Geom {
     i64 osy, osz, osc;
 };
 
+// FP64 instruction selection for the saturated kernels. On GB300 the FP64 pipe issues DFMA
+// at ~1.96 operations/clock/SM but DADD and DMUL at only ~1.65 (measured). Every add,
+// subtract and multiply of the saturated forms is therefore issued as an FMA whose extra
+// operand is a runtime 1.0, -1.0 or -0.0 held in a kernel argument, which the compiler
+// cannot fold back into a DADD/DMUL. The results are bit-identical to the plain
+// operations: the product by +-1 is exact and the FMA rounds once, and adding -0.0 to a
+// product leaves every value (including the sign of zero) unchanged.
+struct Pipe {
+    double one, mone, nz;   // 1.0, -1.0, -0.0
+};
+__device__ __forceinline__ double padd(double a, double b, const Pipe& p) { return fma(a, p.one, b); }
+__device__ __forceinline__ double psub(double a, double b, const Pipe& p) { return fma(b, p.mone, a); }
+__device__ __forceinline__ double pmul(double a, double b, const Pipe& p) { return fma(a, b, p.nz); }
+
 // RHS constants folded on the host (Table I constant folding):
 //   g1 = gamma - 1, nhg1 = -(gamma - 1)/2, s_d = -1/(2 h_d), neps = -eps.
 // The as-written form uses half_h_inv[d] = 1/(2 h_d) as a loop-invariant factor.
@@ -26,12 +40,14 @@ struct RhsConst {
     double sx, sy, sz;             // -1/(2h) per axis (saturated form)
     double hx2i, hy2i, hz2i;       // +1/(2h) per axis (as-written form)
     double neps;
+    Pipe pp;
 };
 
 // Stencil weights: c[d][o-1] and the folded centre weight C0 = -2 sum c.
 struct StarCoef {
     double c[12];
     double c0;
+    Pipe pp;
 };
 
 // Reciprocal of a double for the saturated RHS.
@@ -76,10 +92,38 @@ acs_status ensure_smem(const void* fn, size_t bytes);
 acs_status launch_rhs_plain(const double* U, double* R, const Geom& g, const RhsConst& k, cudaStream_t s);
 acs_status launch_rhs_saturated(const double* U, double* R, const Geom& g, const RhsConst& k,
                                 const acs_tile& t, cudaStream_t s);
+acs_status launch_rhs_ladder(const double* U, double* R, const Geom& g, const RhsConst& k, int form, cudaStream_t s);
 acs_status launch_stencil_plain(const double* u, const double* a, double* out, const Geom& g,
                                 const StarCoef& c, cudaStream_t s);
 acs_status launch_stencil_saturated(const double* u, const double* a, double* out, const Geom& g,
                                     const StarCoef& c, const acs_tile& t, cudaStream_t s);
+
+// Host view of a prepared batch (mirrors acs_batch_plan).
+struct BatchPlanHost {
+    unsigned char* ws;
+    size_t ws_bytes;
+    int kind, n;
+    acs_tile tile;
+    long long total;
+};
+size_t batch_ws_bytes(int n);
+acs_status batch_prepare_host(const acs_batch_item* items, const Geom* geo, int n, int kind, const acs_tile& tile,
+                              unsigned char* ws, size_t ws_bytes, cudaStream_t s, BatchPlanHost& plan);
+acs_status batch_launch(const BatchPlanHost& p, const RhsConst& rk, const StarCoef& sc, cudaStream_t s);
+
+// Autotuner (tune.cu).
+bool tuned_tile(int kind, const Geom& g, acs_tile* t);
+acs_status tune_rhs(const double* U, double* R, const Geom& g, const RhsConst& k, cudaStream_t s, acs_tile* best,
+                    float* best_ms);
+acs_status tune_stencil(const double* u, const double* a, double* out, const Geom& g, const StarCoef& cf,
+                        cudaStream_t s, acs_tile* best, float* best_ms);
+acs_status tune_batch(const acs_batch_item* items, const Geom* geo, int n, int kind, const RhsConst& rk,
+                      const StarCoef& sc, unsigned char* ws, size_t ws_bytes, cudaStream_t s, acs_tile* best,
+                      float* best_ms);
+acs_status tune_cache_save(const char* path);
+acs_status tune_cache_load(const char* path);
+void tune_cache_clear();
+int tune_cache_size();
 
 // Shared-memory bytes and legality of a saturated tile.
 bool rhs_tile_supported(int bx, int by);

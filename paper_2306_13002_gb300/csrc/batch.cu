@@ -1,0 +1,211 @@
+// Batched persistent launch: many grids of uneven sizes in one kernel launch.
+//
+// Every grid of the batch is cut into work units (BX x BY column tile, z-chunk of kchunk
+// planes). A persistent grid of blocks (as many as fit on the GPU at once) pops units from
+// an atomic counter in the caller's workspace and runs the same tile march as the
+// single-grid saturated kernels (march.cuh), so the batch needs one launch however many
+// grids it holds. Grids are ordered largest first, so the long units start early and the
+// small ones fill the tail (longest-processing-time order).
+//
+// Workspace layout (device memory owned by the caller, 16-byte aligned):
+//   [0, 64)                BatchHeader (the work counter, the unit total, the shape)
+//   [64, 64 + n*D)         BatchDesc per grid, in processing order
+//   [.., + 8 (n+1))        prefix sums of the grids' unit counts
+// acs_batch_prepare uploads everything but the counter; acs_batch_launch zeroes the
+// counter with a memset on the stream and launches, so a prepared batch can be launched
+// repeatedly and captured in a CUDA graph (a memset node plus a kernel node).
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "march.cuh"
+
+namespace acs {
+
+struct BatchDesc {
+    const double* in0;  // U (RHS) or u (stencil)
+    const double* in1;  // unused (RHS) or a (stencil)
+    double* out;
+    Geom g;
+    int ntx, nty, nkc, pad;
+};
+
+struct BatchHeader {
+    unsigned long long counter;
+    long long total;
+    int n, kind, bx, by, kchunk, pad0;
+    long long pad1[3];
+};
+static_assert(sizeof(BatchHeader) == 64, "batch header is 64 bytes");
+
+namespace {
+
+constexpr size_t kHeader = 64;
+
+__host__ __device__ inline size_t desc_bytes(int n) { return ((size_t)n * sizeof(BatchDesc) + 15) & ~(size_t)15; }
+
+__device__ __forceinline__ int find_item(const long long* __restrict__ prefix, int n, long long u) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= u)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int BX, int BY, int KIND>
+__global__ void __launch_bounds__(BX * BY, KIND == ACS_KIND_RHS ? RhsShape<BX, BY>::MINB : 1)
+    batch_kernel(const unsigned char* __restrict__ ws, unsigned long long* counter, RhsConst rk, StarCoef sc) {
+    extern __shared__ __align__(16) double smem[];
+    __shared__ long long s_unit;
+    const BatchHeader* h = reinterpret_cast<const BatchHeader*>(ws);
+    const BatchDesc* items = reinterpret_cast<const BatchDesc*>(ws + kHeader);
+    const int n = h->n;
+    const long long* prefix = reinterpret_cast<const long long*>(ws + kHeader + desc_bytes(n));
+    const long long total = h->total;
+    const int kchunk = h->kchunk;
+    const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
+    for (;;) {
+        if (leader) s_unit = (long long)atomicAdd(counter, 1ULL);
+        __syncthreads();
+        const long long u = s_unit;
+        __syncthreads();
+        if (u >= total) break;
+        const int it = find_item(prefix, n, u);
+        const BatchDesc d = items[it];
+        long long lu = u - prefix[it];
+        const int tx = (int)(lu % d.ntx);
+        lu /= d.ntx;
+        const int ty = (int)(lu % d.nty);
+        const int kc = (int)(lu / d.nty);
+        const int k0 = kc * kchunk;
+        const int k1 = min(k0 + kchunk, d.g.nz);
+        if (KIND == ACS_KIND_RHS)
+            rhs_march<BX, BY>(d.in0, d.out, d.g, rk, tx * BX, ty * BY, k0, k1, smem);
+        else
+            star_march<BX, BY>(d.in0, d.in1, d.out, d.g, sc, tx * BX, ty * BY, k0, k1, smem);
+    }
+}
+
+template <int BX, int BY, int KIND>
+acs_status launch_batch_t(const BatchPlanHost& p, unsigned long long* counter, const RhsConst& rk,
+                          const StarCoef& sc, cudaStream_t s) {
+    const size_t smem = KIND == ACS_KIND_RHS ? RhsShape<BX, BY>::BYTES : StarShape<BX, BY>::BYTES;
+    const void* fn = (const void*)batch_kernel<BX, BY, KIND>;
+    acs_status st = ensure_smem(fn, smem);
+    if (st != ACS_OK) return st;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<BX, BY, KIND>, BX * BY, smem) != cudaSuccess)
+        return launch_status("cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (per_sm < 1) return fail(ACS_ERR_UNSUPPORTED, "batch kernel %dx%d does not fit on an SM", BX, BY);
+    long long blocks = (long long)per_sm * num_sms();
+    if (blocks > p.total) blocks = p.total;
+    batch_kernel<BX, BY, KIND><<<(unsigned)blocks, dim3(BX, BY, 1), smem, s>>>(p.ws, counter, rk, sc);
+    return launch_status("batch_kernel");
+}
+
+template <int KIND>
+acs_status dispatch(const BatchPlanHost& p, unsigned long long* counter, const RhsConst& rk, const StarCoef& sc,
+                    cudaStream_t s) {
+    const int bx = p.tile.bx, by = p.tile.by;
+    if (KIND == ACS_KIND_RHS) {
+        if (bx == 32 && by == 8) return launch_batch_t<32, 8, KIND>(p, counter, rk, sc, s);
+        if (bx == 32 && by == 4) return launch_batch_t<32, 4, KIND>(p, counter, rk, sc, s);
+        if (bx == 32 && by == 16) return launch_batch_t<32, 16, KIND>(p, counter, rk, sc, s);
+        if (bx == 16 && by == 8) return launch_batch_t<16, 8, KIND>(p, counter, rk, sc, s);
+        if (bx == 16 && by == 16) return launch_batch_t<16, 16, KIND>(p, counter, rk, sc, s);
+        if (bx == 64 && by == 4) return launch_batch_t<64, 4, KIND>(p, counter, rk, sc, s);
+    } else {
+        if (bx == 32 && by == 8) return launch_batch_t<32, 8, KIND>(p, counter, rk, sc, s);
+        if (bx == 32 && by == 4) return launch_batch_t<32, 4, KIND>(p, counter, rk, sc, s);
+        if (bx == 32 && by == 16) return launch_batch_t<32, 16, KIND>(p, counter, rk, sc, s);
+        if (bx == 64 && by == 4) return launch_batch_t<64, 4, KIND>(p, counter, rk, sc, s);
+        if (bx == 64 && by == 8) return launch_batch_t<64, 8, KIND>(p, counter, rk, sc, s);
+        if (bx == 16 && by == 16) return launch_batch_t<16, 16, KIND>(p, counter, rk, sc, s);
+    }
+    return fail(ACS_ERR_UNSUPPORTED, "batch tile %dx%d is not built", bx, by);
+}
+
+}  // namespace
+
+size_t batch_ws_bytes(int n) { return n < 1 ? 0 : kHeader + desc_bytes(n) + sizeof(long long) * (size_t)(n + 1); }
+
+// Host half of acs_batch_prepare: geometry already validated; builds the packed image.
+acs_status batch_pack(const acs_batch_item* items, const Geom* geo, int n, int kind, const acs_tile& tile,
+                      std::vector<unsigned char>& image, long long& total) {
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::vector<long long> units(n);
+    for (int q = 0; q < n; ++q) {
+        const Geom& g = geo[q];
+        const long long ntx = (g.nx + tile.bx - 1) / tile.bx, nty = (g.ny + tile.by - 1) / tile.by;
+        const long long nkc = (g.nz + tile.kchunk - 1) / tile.kchunk;
+        units[q] = ntx * nty * nkc;
+    }
+    auto points = [&](int q) { return (long long)geo[q].nx * geo[q].ny * geo[q].nz; };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return points(x) > points(y); });
+    image.assign(batch_ws_bytes(n), 0);
+    BatchHeader h;
+    std::memset(&h, 0, sizeof(h));
+    h.n = n;
+    h.kind = kind;
+    h.bx = tile.bx;
+    h.by = tile.by;
+    h.kchunk = tile.kchunk;
+    BatchDesc* d = reinterpret_cast<BatchDesc*>(image.data() + kHeader);
+    long long* prefix = reinterpret_cast<long long*>(image.data() + kHeader + desc_bytes(n));
+    long long acc = 0;
+    for (int r = 0; r < n; ++r) {
+        const int q = order[r];
+        const Geom& g = geo[q];
+        BatchDesc e;
+        std::memset(&e, 0, sizeof(e));
+        e.in0 = items[q].in0;
+        e.in1 = items[q].in1;
+        e.out = items[q].out;
+        e.g = g;
+        e.ntx = (g.nx + tile.bx - 1) / tile.bx;
+        e.nty = (g.ny + tile.by - 1) / tile.by;
+        e.nkc = (g.nz + tile.kchunk - 1) / tile.kchunk;
+        d[r] = e;
+        prefix[r] = acc;
+        acc += units[q];
+    }
+    prefix[n] = acc;
+    h.total = acc;
+    std::memcpy(image.data(), &h, sizeof(h));
+    total = acc;
+    return ACS_OK;
+}
+
+acs_status batch_prepare_host(const acs_batch_item* items, const Geom* geo, int n, int kind, const acs_tile& tile,
+                              unsigned char* ws, size_t ws_bytes, cudaStream_t s, BatchPlanHost& plan) {
+    std::vector<unsigned char> image;
+    long long total = 0;
+    acs_status st = batch_pack(items, geo, n, kind, tile, image, total);
+    if (st != ACS_OK) return st;
+    if (image.size() > ws_bytes) return fail(ACS_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, image.size());
+    if (cudaMemcpyAsync(ws, image.data(), image.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return launch_status("cudaMemcpyAsync");
+    if (cudaStreamSynchronize(s) != cudaSuccess) return launch_status("cudaStreamSynchronize");
+    plan.ws = ws;
+    plan.ws_bytes = ws_bytes;
+    plan.kind = kind;
+    plan.n = n;
+    plan.tile = tile;
+    plan.total = total;
+    return ACS_OK;
+}
+
+acs_status batch_launch(const BatchPlanHost& p, const RhsConst& rk, const StarCoef& sc, cudaStream_t s) {
+    unsigned long long* counter = reinterpret_cast<unsigned long long*>(p.ws);
+    if (cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s) != cudaSuccess) return launch_status("cudaMemsetAsync");
+    if (p.kind == ACS_KIND_RHS) return dispatch<ACS_KIND_RHS>(p, counter, rk, sc, s);
+    return dispatch<ACS_KIND_STENCIL>(p, counter, rk, sc, s);
+}
+
+}  // namespace acs

@@ -1,0 +1,254 @@
+// Tile marches of the two saturated loop bodies, shared by the single-grid kernels and the
+// persistent batch kernel. See rhs_saturated.cu and stencil.cu for the derivations.
+#pragma once
+
+#include "acs_internal.cuh"
+
+namespace acs {
+
+template <int BX, int BY>
+struct RhsShape {
+    static constexpr int PX = BX + 4, PY = BY + 4, PLANE = PX * PY;
+    static constexpr int NSLOT = 5;
+    static constexpr int U_ELEMS = NSLOT * 5 * PLANE;
+    static constexpr int FX_ELEMS = 4 * BY * (BX + 2);
+    static constexpr int FY_ELEMS = 4 * (BY + 2) * BX;
+    static constexpr size_t BYTES = sizeof(double) * (size_t)(U_ELEMS + FX_ELEMS + FY_ELEMS);
+    static constexpr int NT = BX * BY;
+    static constexpr int MINB = NT <= 256 ? 2 : 1;
+};
+
+// The 12 non-trivial flux values of one point (component 0 of F_d is m_d itself).
+// fx = F_x[1..4], fy = F_y[1..4], fz = F_z[1..4]. Every caller uses this one definition,
+// so a flux value is bit-identical whichever thread computes it.
+__device__ __forceinline__ void point_flux(double rho, double mx, double my, double mz, double E, const RhsConst& k,
+                                           double fx[4], double fy[4], double fz[4]) {
+    const Pipe& q = k.pp;
+    const double r = rcp_refined(rho);
+    const double vx = pmul(mx, r, q), vy = pmul(my, r, q), vz = pmul(mz, r, q);
+    const double mxvx = pmul(mx, vx, q);
+    const double twoKE = fma(mz, vz, fma(my, vy, mxvx));
+    const double P = fma(k.nhg1, twoKE, pmul(k.g1, E, q));
+    const double EP = padd(E, P, q);
+    const double oxy = pmul(mx, vy, q), oxz = pmul(mx, vz, q), oyz = pmul(my, vz, q);
+    fx[0] = padd(mxvx, P, q);
+    fx[1] = oxy;
+    fx[2] = oxz;
+    fx[3] = pmul(EP, vx, q);
+    fy[0] = oxy;
+    fy[1] = fma(my, vy, P);
+    fy[2] = oyz;
+    fy[3] = pmul(EP, vy, q);
+    fz[0] = oxz;
+    fz[1] = oyz;
+    fz[2] = fma(mz, vz, P);
+    fz[3] = pmul(EP, vz, q);
+}
+
+// Copy plane q (interior z index, q >= -2) of all five components, with a 2-cell xy halo,
+// into one ring slot. Only cells with x < nx+2 and y < ny+2 (interior coordinates) are
+// copied; the rest of the slot is never read by an active point.
+template <int BX, int BY>
+__device__ __forceinline__ void load_plane(double* slot, const double* __restrict__ U, const Geom& g, int i0, int j0,
+                                           int q, int tid) {
+    using S = RhsShape<BX, BY>;
+    const i64 zoff = (i64)(q + g.halo) * g.isz;
+    const int xlim = min(S::PX, g.nx + 4 - i0);
+    const int ylim = min(S::PY, g.ny + 4 - j0);
+    const double* base = U + zoff + (i64)(j0 - 2 + g.halo) * g.isy + (i0 - 2 + g.halo);
+#pragma unroll 1
+    for (int e = tid; e < 5 * S::PLANE; e += S::NT) {
+        const int c = e / S::PLANE;
+        const int r = e - c * S::PLANE;
+        const int yy = r / S::PX;
+        const int xx = r - yy * S::PX;
+        if (xx < xlim && yy < ylim) cp_async8(slot + e, base + (i64)c * g.isc + (i64)yy * g.isy + xx);
+    }
+}
+
+// One block's work: the BX x BY column tile at (i0, j0), z-planes [k0, k1). Ends with all
+// threads past a barrier after their last shared-memory read, so the caller may reuse smem.
+template <int BX, int BY>
+__device__ __forceinline__ void rhs_march(const double* __restrict__ U, double* __restrict__ R, const Geom& g,
+                                          const RhsConst& k, int i0, int j0, int k0, int k1, double* smem) {
+    using S = RhsShape<BX, BY>;
+    constexpr int PX = S::PX, PLANE = S::PLANE;
+    double* Us = smem;
+    double* Fxs = smem + S::U_ELEMS;
+    double* Fys = Fxs + S::FX_ELEMS;
+
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+    const int i = i0 + tx, j = j0 + ty;
+    const bool active = (i < g.nx) && (j < g.ny);
+    const int own = (ty + 2) * PX + (tx + 2);
+    auto slot = [&](int q) -> double* { return Us + ((q + S::NSLOT) % S::NSLOT) * (5 * PLANE); };
+
+    // Prologue: planes k0-2 .. k0+2.
+    for (int q = k0 - 2; q <= k0 + 2; ++q) load_plane<BX, BY>(slot(q), U, g, i0, j0, q, tid);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+
+    double fzm[4], fz0[4], fzp[4], pfx[4], pfy[4];
+    {
+        const double* s = slot(k0 - 1);
+        double ux[4], uy[4];
+        point_flux(s[own], s[PLANE + own], s[2 * PLANE + own], s[3 * PLANE + own], s[4 * PLANE + own], k, ux, uy, fzm);
+        s = slot(k0);
+        point_flux(s[own], s[PLANE + own], s[2 * PLANE + own], s[3 * PLANE + own], s[4 * PLANE + own], k, pfx, pfy, fz0);
+    }
+
+    for (int kk = k0; kk < k1; ++kk) {
+        const double* s0 = slot(kk);
+        // (1) x/y fluxes of plane kk: own point (computed one step earlier) and the ring.
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            Fxs[(c * BY + ty) * (BX + 2) + tx + 1] = pfx[c];
+            Fys[(c * (BY + 2) + ty + 1) * BX + tx] = pfy[c];
+        }
+        if (tid < 2 * (BX + BY)) {
+            int rx, ry;
+            const bool isx = tid < 2 * BY;
+            if (isx) {
+                ry = tid >> 1;
+                rx = (tid & 1) ? BX : -1;
+            } else {
+                const int t = tid - 2 * BY;
+                rx = t >> 1;
+                ry = (t & 1) ? BY : -1;
+            }
+            const int e = (ry + 2) * PX + (rx + 2);
+            double fx[4], fy[4], fz[4];
+            point_flux(s0[e], s0[PLANE + e], s0[2 * PLANE + e], s0[3 * PLANE + e], s0[4 * PLANE + e], k, fx, fy, fz);
+            if (isx) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) Fxs[(c * BY + ry) * (BX + 2) + rx + 1] = fx[c];
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) Fys[(c * (BY + 2) + ry + 1) * BX + rx] = fy[c];
+            }
+        }
+        // (2) all fluxes of the own point at plane kk+1.
+        {
+            const double* s = slot(kk + 1);
+            point_flux(s[own], s[PLANE + own], s[2 * PLANE + own], s[3 * PLANE + own], s[4 * PLANE + own], k, pfx, pfy,
+                       fzp);
+        }
+        cp_async_wait_all();  // plane kk+2 (issued one step earlier) has landed
+        __syncthreads();
+
+        // (3) the right-hand side at plane kk.
+        if (active) {
+            const double* sm1 = slot(kk - 1);
+            const double* sp1 = slot(kk + 1);
+            const double* sm2 = slot(kk - 2);
+            const double* sp2 = slot(kk + 2);
+            double* Rp = R + (i64)kk * g.osz + (i64)j * g.osy + i;
+            const Pipe& q = k.pp;
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                const int cb = c * PLANE + own;
+                double fxd, fyd, fzd;
+                if (c == 0) {
+                    fxd = psub(s0[PLANE + own + 1], s0[PLANE + own - 1], q);
+                    fyd = psub(s0[2 * PLANE + own + PX], s0[2 * PLANE + own - PX], q);
+                    fzd = psub(sp1[3 * PLANE + own], sm1[3 * PLANE + own], q);
+                } else {
+                    const double* fxr = Fxs + ((c - 1) * BY + ty) * (BX + 2) + tx;
+                    fxd = psub(fxr[2], fxr[0], q);
+                    fyd = psub(Fys[((c - 1) * (BY + 2) + ty + 2) * BX + tx], Fys[((c - 1) * (BY + 2) + ty) * BX + tx], q);
+                    fzd = psub(fzp[c - 1], fzm[c - 1], q);
+                }
+                double fl = pmul(fxd, k.sx, q);
+                fl = fma(fyd, k.sy, fl);
+                fl = fma(fzd, k.sz, fl);
+                const double s2 = padd(padd(padd(s0[cb - 2], s0[cb + 2], q), padd(s0[cb - 2 * PX], s0[cb + 2 * PX], q), q),
+                                       padd(sm2[cb], sp2[cb], q), q);
+                const double s1 = padd(padd(padd(s0[cb - 1], s0[cb + 1], q), padd(s0[cb - PX], s0[cb + PX], q), q),
+                                       padd(sm1[cb], sp1[cb], q), q);
+                double dd = fma(-4.0, s1, s2);
+                dd = fma(18.0, s0[cb], dd);
+                Rp[(i64)c * g.osc] = fma(k.neps, dd, fl);
+            }
+        }
+        // (4) rotate the z-flux queue.
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            fzm[c] = fz0[c];
+            fz0[c] = fzp[c];
+        }
+        __syncthreads();  // slot kk-2 and the flux planes are free again
+        // (5) bulk-load plane kk+3 into the slot of kk-2.
+        if (kk + 3 <= k1 + 1) load_plane<BX, BY>(slot(kk + 3), U, g, i0, j0, kk + 3, tid);
+        cp_async_commit();
+    }
+    cp_async_wait_all();
+}
+
+template <int BX, int BY>
+struct StarShape {
+    static constexpr int PX = BX + 8, PY = BY + 8, PLANE = PX * PY;
+    static constexpr int NSLOT = 10;
+    static constexpr size_t BYTES = sizeof(double) * (size_t)NSLOT * PLANE;
+    static constexpr int NT = BX * BY;
+};
+
+template <int BX, int BY>
+__device__ __forceinline__ void load_star_plane(double* slot, const double* __restrict__ u, const Geom& g, int i0,
+                                                int j0, int q, int tid) {
+    using S = StarShape<BX, BY>;
+    const int xlim = min(S::PX, g.nx + 8 - i0);
+    const int ylim = min(S::PY, g.ny + 8 - j0);
+    const double* base = u + (i64)(q + g.halo) * g.isz + (i64)(j0 - 4 + g.halo) * g.isy + (i0 - 4 + g.halo);
+#pragma unroll 1
+    for (int e = tid; e < S::PLANE; e += S::NT) {
+        const int yy = e / S::PX;
+        const int xx = e - yy * S::PX;
+        if (xx < xlim && yy < ylim) cp_async8(slot + e, base + (i64)yy * g.isy + xx);
+    }
+}
+
+// One block's work: the BX x BY column tile at (i0, j0), z-planes [k0, k1). Ends with all
+// threads past a barrier after their last shared-memory read.
+template <int BX, int BY>
+__device__ __forceinline__ void star_march(const double* __restrict__ u, const double* __restrict__ a,
+                                           double* __restrict__ out, const Geom& g, const StarCoef& cf, int i0, int j0,
+                                           int k0, int k1, double* smem) {
+    using S = StarShape<BX, BY>;
+    constexpr int PX = S::PX, PLANE = S::PLANE;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+    const int i = i0 + tx, j = j0 + ty;
+    const bool active = (i < g.nx) && (j < g.ny);
+    const int own = (ty + 4) * PX + (tx + 4);
+    auto slot = [&](int q) -> double* { return smem + ((q + S::NSLOT) % S::NSLOT) * PLANE; };
+
+    for (int q = k0 - 4; q <= k0 + 4; ++q) load_star_plane<BX, BY>(slot(q), u, g, i0, j0, q, tid);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+
+    const double* ap = a + (i64)(k0 + g.halo) * g.isz + (i64)(j + g.halo) * g.isy + (i + g.halo);
+    for (int kk = k0; kk < k1; ++kk) {
+        // Bulk-load the plane the next step needs into the slot of plane kk-5.
+        if (kk + 5 <= k1 + 3) load_star_plane<BX, BY>(slot(kk + 5), u, g, i0, j0, kk + 5, tid);
+        cp_async_commit();
+        if (active) {
+            const double av = __ldg(ap);
+            const double* s0 = slot(kk);
+            const Pipe& q = cf.pp;
+            double t = pmul(cf.c0, s0[own], q);
+#pragma unroll
+            for (int o = 1; o <= 4; ++o) t = fma(cf.c[o - 1], padd(s0[own + o], s0[own - o], q), t);
+#pragma unroll
+            for (int o = 1; o <= 4; ++o) t = fma(cf.c[4 + o - 1], padd(s0[own + o * PX], s0[own - o * PX], q), t);
+#pragma unroll
+            for (int o = 1; o <= 4; ++o) t = fma(cf.c[8 + o - 1], padd(slot(kk + o)[own], slot(kk - o)[own], q), t);
+            out[(i64)kk * g.osz + (i64)j * g.osy + i] = pmul(av, t, q);
+        }
+        ap += g.isz;
+        cp_async_wait_all();
+        __syncthreads();
+    }
+}
+
+}  // namespace acs

@@ -10,10 +10,11 @@
 //   C0 = -2 sum c  (folded on the host: constant folding),
 // i.e. the common factor a(p) is pulled out of the twelve terms (distributivity expressed
 // through ASSOC/COMM and FMA1), the twelve copies of -2u(p) merge into one term, and each
-// pair of symmetric neighbours is summed before its single FMA. The xy-planes of u with a
+// pair of symmetric neighbours is summed before its single FMA. Adds and multiplies are
+// issued as FMAs with runtime +-1 / -0 operands (faster on GB300, bit-identical). The xy-planes of u with a
 // 4-cell halo live in a ten-slot shared-memory ring: the nine planes k-4..k+4 in use plus
 // the plane being prefetched with cp.async for the next step.
-#include "acs_internal.cuh"
+#include "march.cuh"
 
 namespace acs {
 namespace {
@@ -40,71 +41,13 @@ __global__ void __launch_bounds__(256) star_plain_kernel(const double* u, const 
 }
 
 template <int BX, int BY>
-struct StarShape {
-    static constexpr int PX = BX + 8, PY = BY + 8, PLANE = PX * PY;
-    static constexpr int NSLOT = 10;
-    static constexpr size_t BYTES = sizeof(double) * (size_t)NSLOT * PLANE;
-    static constexpr int NT = BX * BY;
-};
-
-template <int BX, int BY>
-__device__ __forceinline__ void load_star_plane(double* slot, const double* __restrict__ u, const Geom& g, int i0,
-                                                int j0, int q, int tid) {
-    using S = StarShape<BX, BY>;
-    const int xlim = min(S::PX, g.nx + 8 - i0);
-    const int ylim = min(S::PY, g.ny + 8 - j0);
-    const double* base = u + (i64)(q + g.halo) * g.isz + (i64)(j0 - 4 + g.halo) * g.isy + (i0 - 4 + g.halo);
-#pragma unroll 1
-    for (int e = tid; e < S::PLANE; e += S::NT) {
-        const int yy = e / S::PX;
-        const int xx = e - yy * S::PX;
-        if (xx < xlim && yy < ylim) cp_async8(slot + e, base + (i64)yy * g.isy + xx);
-    }
-}
-
-template <int BX, int BY>
 __global__ void __launch_bounds__(BX * BY) star_saturated_kernel(const double* __restrict__ u,
                                                                  const double* __restrict__ a,
                                                                  double* __restrict__ out, Geom g, StarCoef cf,
                                                                  int kchunk) {
-    using S = StarShape<BX, BY>;
-    constexpr int PX = S::PX, PLANE = S::PLANE;
     extern __shared__ __align__(16) double smem[];
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
-    const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
     const int k0 = blockIdx.z * kchunk;
-    const int k1 = min(k0 + kchunk, g.nz);
-    const int i = i0 + tx, j = j0 + ty;
-    const bool active = (i < g.nx) && (j < g.ny);
-    const int own = (ty + 4) * PX + (tx + 4);
-    auto slot = [&](int q) -> double* { return smem + ((q + S::NSLOT) % S::NSLOT) * PLANE; };
-
-    for (int q = k0 - 4; q <= k0 + 4; ++q) load_star_plane<BX, BY>(slot(q), u, g, i0, j0, q, tid);
-    cp_async_commit();
-    cp_async_wait_all();
-    __syncthreads();
-
-    const double* ap = a + (i64)(k0 + g.halo) * g.isz + (i64)(j + g.halo) * g.isy + (i + g.halo);
-    for (int kk = k0; kk < k1; ++kk) {
-        // Bulk-load the plane the next step needs into the slot of plane kk-5.
-        if (kk + 5 <= k1 + 3) load_star_plane<BX, BY>(slot(kk + 5), u, g, i0, j0, kk + 5, tid);
-        cp_async_commit();
-        if (active) {
-            const double av = __ldg(ap);
-            const double* s0 = slot(kk);
-            double t = cf.c0 * s0[own];
-#pragma unroll
-            for (int o = 1; o <= 4; ++o) t = fma(cf.c[o - 1], s0[own + o] + s0[own - o], t);
-#pragma unroll
-            for (int o = 1; o <= 4; ++o) t = fma(cf.c[4 + o - 1], s0[own + o * PX] + s0[own - o * PX], t);
-#pragma unroll
-            for (int o = 1; o <= 4; ++o) t = fma(cf.c[8 + o - 1], slot(kk + o)[own] + slot(kk - o)[own], t);
-            out[(i64)kk * g.osz + (i64)j * g.osy + i] = av * t;
-        }
-        ap += g.isz;
-        cp_async_wait_all();
-        __syncthreads();
-    }
+    star_march<BX, BY>(u, a, out, g, cf, blockIdx.x * BX, blockIdx.y * BY, k0, min(k0 + kchunk, g.nz), smem);
 }
 
 template <int BX, int BY>

@@ -1,0 +1,210 @@
+// Launch-shape autotuner for the saturated kernels and the batch launch.
+//
+// The paper leaves the parallel structure to the directive compiler and notes that the
+// shape of the parallelism decides performance (Sec. II-C). Here the shape is ours to
+// choose: the tuner times every built tile (BX x BY) with a few z-chunk lengths on the
+// caller's own buffers (CUDA events on the caller's stream, best of three launches after a
+// warm-up), and records the fastest per workload shape in a process-wide cache. A saturated
+// call with tile == NULL uses the cached shape for its grid size when there is one.
+// Tuning overwrites the output buffers and synchronises the stream; it cannot be captured.
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "acs_internal.cuh"
+
+namespace acs {
+namespace {
+
+struct Entry {
+    acs_tile tile;
+    float ms;
+};
+std::mutex g_mu;
+std::map<std::string, Entry> g_cache;
+
+std::string key_of(int kind, const Geom* g, int n) {
+    std::string k = std::to_string(kind) + ":";
+    for (int q = 0; q < n; ++q) {
+        char buf[64];
+        snprintf(buf, sizeof(buf), "%dx%dx%d;", g[q].nx, g[q].ny, g[q].nz);
+        k += buf;
+    }
+    return k;
+}
+
+const int kRhsTiles[][2] = {{32, 8}, {32, 4}, {32, 16}, {16, 8}, {16, 16}, {64, 4}};
+const int kStarTiles[][2] = {{32, 8}, {32, 4}, {32, 16}, {64, 4}, {64, 8}, {16, 16}};
+const int kChunks[] = {8, 16, 32, 64};
+
+struct Timer {
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~Timer() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+    bool init() { return cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess; }
+};
+
+// Time `run` (which launches on s): one warm-up, then the best of three launches.
+template <class F>
+acs_status time_best(F run, cudaStream_t s, Timer& t, float& ms) {
+    acs_status st = run();
+    if (st != ACS_OK) return st;
+    ms = 1e30f;
+    for (int r = 0; r < 3; ++r) {
+        if (cudaEventRecord(t.a, s) != cudaSuccess) return launch_status("cudaEventRecord");
+        st = run();
+        if (st != ACS_OK) return st;
+        if (cudaEventRecord(t.b, s) != cudaSuccess) return launch_status("cudaEventRecord");
+        if (cudaEventSynchronize(t.b) != cudaSuccess) return launch_status("cudaEventSynchronize");
+        float e = 0.f;
+        if (cudaEventElapsedTime(&e, t.a, t.b) != cudaSuccess) return launch_status("cudaEventElapsedTime");
+        if (e < ms) ms = e;
+    }
+    return ACS_OK;
+}
+
+template <class Launch>
+acs_status tune_grid(int kind, const Geom& g, const int (*tiles)[2], int ntiles, Launch launch, cudaStream_t s,
+                     acs_tile* best, float* best_ms) {
+    Timer t;
+    if (!t.init()) return launch_status("cudaEventCreate");
+    acs_tile bt = {0, 0, 0, 0};
+    float bms = 1e30f;
+    for (int q = 0; q < ntiles; ++q) {
+        for (int kc : kChunks) {
+            if (kc > g.nz && kc != kChunks[0]) continue;
+            acs_tile cand = {tiles[q][0], tiles[q][1], kc, 0};
+            float ms = 0.f;
+            acs_status st = time_best([&]() { return launch(cand); }, s, t, ms);
+            if (st != ACS_OK) return st;
+            if (ms < bms) {
+                bms = ms;
+                bt = cand;
+            }
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_cache[key_of(kind, &g, 1)] = Entry{bt, bms};
+    }
+    if (best) *best = bt;
+    if (best_ms) *best_ms = bms;
+    return ACS_OK;
+}
+
+}  // namespace
+
+bool tuned_tile(int kind, const Geom& g, acs_tile* t) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_cache.find(key_of(kind, &g, 1));
+    if (it == g_cache.end()) return false;
+    *t = it->second.tile;
+    return true;
+}
+
+acs_status tune_rhs(const double* U, double* R, const Geom& g, const RhsConst& k, cudaStream_t s, acs_tile* best,
+                    float* best_ms) {
+    return tune_grid(
+        ACS_KIND_RHS, g, kRhsTiles, 6, [&](const acs_tile& c) { return launch_rhs_saturated(U, R, g, k, c, s); }, s, best,
+        best_ms);
+}
+
+acs_status tune_stencil(const double* u, const double* a, double* out, const Geom& g, const StarCoef& cf,
+                        cudaStream_t s, acs_tile* best, float* best_ms) {
+    return tune_grid(
+        ACS_KIND_STENCIL, g, kStarTiles, 6,
+        [&](const acs_tile& c) { return launch_stencil_saturated(u, a, out, g, cf, c, s); }, s, best, best_ms);
+}
+
+acs_status tune_batch(const acs_batch_item* items, const Geom* geo, int n, int kind, const RhsConst& rk,
+                      const StarCoef& sc, unsigned char* ws, size_t ws_bytes, cudaStream_t s, acs_tile* best,
+                      float* best_ms) {
+    Timer t;
+    if (!t.init()) return launch_status("cudaEventCreate");
+    const int(*tiles)[2] = kind == ACS_KIND_RHS ? kRhsTiles : kStarTiles;
+    acs_tile bt = {0, 0, 0, 0};
+    float bms = 1e30f;
+    static const int chunks[] = {4, 8, 16, 32};
+    for (int q = 0; q < 6; ++q) {
+        for (int kc : chunks) {
+            acs_tile cand = {tiles[q][0], tiles[q][1], kc, 0};
+            BatchPlanHost plan;
+            acs_status st = batch_prepare_host(items, geo, n, kind, cand, ws, ws_bytes, s, plan);
+            if (st != ACS_OK) return st;
+            float ms = 0.f;
+            st = time_best([&]() { return batch_launch(plan, rk, sc, s); }, s, t, ms);
+            if (st != ACS_OK) return st;
+            if (ms < bms) {
+                bms = ms;
+                bt = cand;
+            }
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_cache[key_of(kind + 2, geo, n)] = Entry{bt, bms};
+    }
+    if (best) *best = bt;
+    if (best_ms) *best_ms = bms;
+    return ACS_OK;
+}
+
+acs_status tune_cache_save(const char* path) {
+    FILE* f = fopen(path, "w");
+    if (!f) return fail(ACS_ERR_INVALID, "cannot open %s for writing", path);
+    std::lock_guard<std::mutex> lk(g_mu);
+    fprintf(f, "acs-tune-cache 1\n");
+    for (auto& kv : g_cache)
+        fprintf(f, "%d %d %d %.6f %s\n", kv.second.tile.bx, kv.second.tile.by, kv.second.tile.kchunk, kv.second.ms,
+                kv.first.c_str());
+    fclose(f);
+    return ACS_OK;
+}
+
+acs_status tune_cache_load(const char* path) {
+    FILE* f = fopen(path, "r");
+    if (!f) return fail(ACS_ERR_INVALID, "cannot open %s", path);
+    char line[4096];
+    if (!fgets(line, sizeof(line), f) || strncmp(line, "acs-tune-cache 1", 16) != 0) {
+        fclose(f);
+        return fail(ACS_ERR_INVALID, "%s is not an autotune cache (version 1)", path);
+    }
+    std::map<std::string, Entry> loaded;
+    while (fgets(line, sizeof(line), f)) {
+        int bx, by, kc;
+        float ms;
+        char key[4000];
+        if (sscanf(line, "%d %d %d %f %3999s", &bx, &by, &kc, &ms, key) != 5) {
+            fclose(f);
+            return fail(ACS_ERR_INVALID, "malformed autotune cache line: %s", line);
+        }
+        const bool rhs_key = key[0] == '0' || key[0] == '2';
+        const bool ok = rhs_key ? rhs_tile_supported(bx, by) : star_tile_supported(bx, by);
+        if (!ok || kc < 1) {
+            fclose(f);
+            return fail(ACS_ERR_INVALID, "autotune cache names an unbuilt tile %dx%d", bx, by);
+        }
+        loaded[key] = Entry{acs_tile{bx, by, kc, 0}, ms};
+    }
+    fclose(f);
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto& kv : loaded) g_cache[kv.first] = kv.second;
+    return ACS_OK;
+}
+
+void tune_cache_clear() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_cache.clear();
+}
+
+int tune_cache_size() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    return (int)g_cache.size();
+}
+
+}  // namespace acs

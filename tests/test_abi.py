@@ -108,3 +108,40 @@ def test_stencil_rejects_bad_arguments(lib):
     assert lib.acs_stencil_saturated(FAKE_U, A, FAKE_R, ctypes.byref(g), bad, None, None) == 1
     t = binding.Tile(48, 8, 0, 0)
     assert lib.acs_stencil_saturated(FAKE_U, A, FAKE_R, ctypes.byref(g), c, ctypes.byref(t), None) == 4
+
+
+def test_batch_prepare_rejects_bad_arguments(lib):
+    g = _grid(halo=4, comp=False)
+    A = FAKE_U + 0x1000000
+    items = (binding.BatchItem * 2)(binding.BatchItem(FAKE_U, A, FAKE_R, g), binding.BatchItem(FAKE_U, A, FAKE_R, g))
+    plan = binding.BatchPlan()
+    need = binding.acs_batch_workspace_bytes(2)
+    assert need > 0 and binding.acs_batch_workspace_bytes(0) == 0
+    WS = 0x70000000
+    st = lib.acs_batch_prepare(items, 2, 1, None, WS, need - 1, ctypes.byref(plan), None)
+    assert st == 8                                                    # workspace too small
+    assert lib.acs_batch_prepare(items, 2, 1, None, WS + 8, need, ctypes.byref(plan), None) == 2   # misaligned
+    assert lib.acs_batch_prepare(items, 2, 1, None, None, need, ctypes.byref(plan), None) == 8
+    assert lib.acs_batch_prepare(items, 0, 1, None, WS, need, ctypes.byref(plan), None) == 1
+    assert lib.acs_batch_prepare(items, 2, 7, None, WS, need, ctypes.byref(plan), None) == 1
+    assert lib.acs_batch_prepare(None, 2, 1, None, WS, need, ctypes.byref(plan), None) == 1
+    bad = (binding.BatchItem * 1)(binding.BatchItem(FAKE_U, A, A + 80, g))
+    assert lib.acs_batch_prepare(bad, 1, 1, None, WS, need, ctypes.byref(plan), None) == 7     # alias
+    t = binding.Tile(24, 8, 8, 0)
+    assert lib.acs_batch_prepare(items, 2, 1, ctypes.byref(t), WS, need, ctypes.byref(plan), None) == 4
+
+
+def test_batch_launch_rejects_unprepared_plan(lib):
+    plan = binding.BatchPlan()
+    c = (ctypes.c_double * 12)(*([1.0] * 12))
+    assert lib.acs_batch_launch(ctypes.byref(plan), ctypes.cast(c, ctypes.c_void_p), None) == 1
+    assert lib.acs_batch_launch(None, None, None) == 1
+
+
+def test_tune_cache_file_errors(lib, tmp_path):
+    assert lib.acs_tune_cache_load(str(tmp_path / "missing.txt").encode()) == 1
+    p = tmp_path / "x.txt"
+    p.write_text("not a cache\n")
+    assert lib.acs_tune_cache_load(str(p).encode()) == 1
+    lib.acs_tune_cache_clear()
+    assert lib.acs_tune_cache_size() == 0

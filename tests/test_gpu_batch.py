@@ -1,0 +1,163 @@
+"""GPU tests of the batched persistent launch, its CUDA-graph capture and the autotuner."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2306_13002_gb300 import binding, inputs
+from _parity import assert_parity, to_dev
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _stencil_batch(sides, seed0):
+    grids, host = [], []
+    for q, (nx, ny, nz) in enumerate(sides):
+        u, a = inputs.stencil_fields(int(nx), int(ny), int(nz), halo=4, seed=seed0 + q)
+        out = torch.full((int(nz), int(ny), int(nx)), float("nan"), dtype=torch.float64, device="cuda")
+        grids.append((to_dev(u), to_dev(a), out))
+        host.append((u, a))
+    return grids, host
+
+
+def _ws(n):
+    nbytes = binding.acs_batch_workspace_bytes(n)
+    return torch.zeros((nbytes + 15) // 16 * 2, dtype=torch.float64, device="cuda")
+
+
+def test_stencil_batch_64_uneven_grids_matches_oracle():
+    """64 grids, sides log-uniform in [16, 160] per axis, one persistent launch."""
+    sides = inputs.batch_sides(64, seed=inputs.SEED_BATCH)
+    grids, host = _stencil_batch(sides, 7000)
+    ws = _ws(len(grids))
+    plan = binding.acs_batch_prepare(binding.KIND_STENCIL, grids, ws)
+    binding.acs_batch_launch(plan)
+    torch.cuda.synchronize()
+    for (u, a), (_, _, out) in zip(host, grids):
+        assert_parity(out.cpu().numpy(), oracle.stencil(u, a, threads=8), what=f"batch grid {u.shape}")
+
+
+@pytest.mark.parametrize("tile", [None, (32, 4, 4), (16, 16, 32), (64, 8, 8)])
+def test_stencil_batch_tiles(tile):
+    sides = [(5, 3, 2), (40, 17, 9), (1, 1, 1), (33, 70, 12), (64, 8, 30)]
+    grids, host = _stencil_batch(sides, 7100)
+    plan = binding.acs_batch_prepare(binding.KIND_STENCIL, grids, _ws(len(grids)), tile=tile)
+    binding.acs_batch_launch(plan)
+    torch.cuda.synchronize()
+    for (u, a), (_, _, out) in zip(host, grids):
+        assert_parity(out.cpu().numpy(), oracle.stencil(u, a), what=f"batch {tile} grid {u.shape}")
+
+
+@pytest.mark.parametrize("tile", [None, (16, 8, 4), (32, 16, 8)])
+def test_rhs_batch_matches_oracle(tile):
+    rng = np.random.default_rng(11)
+    sides = rng.integers(1, 60, size=(10, 3))
+    grids, host = [], []
+    for q, (nx, ny, nz) in enumerate(sides):
+        U = inputs.rhs_field(int(nx), int(ny), int(nz), halo=2, seed=7200 + q)
+        R = torch.full((5, int(nz), int(ny), int(nx)), float("nan"), dtype=torch.float64, device="cuda")
+        grids.append((to_dev(U), None, R))
+        host.append(U)
+    params = {"gamma": 1.4, "eps": 0.25, "h": (1.0, 0.5, 2.0)}
+    plan = binding.acs_batch_prepare(binding.KIND_RHS, grids, _ws(len(grids)), tile=tile)
+    binding.acs_batch_launch(plan, params)
+    torch.cuda.synchronize()
+    for U, (_, _, R) in zip(host, grids):
+        assert_parity(R.cpu().numpy(), oracle.rhs(U, h=(1.0, 0.5, 2.0)), what=f"rhs batch {U.shape}")
+
+
+def test_batch_in_cuda_graph_replays():
+    """Capture acs_batch_launch once; replay after changing the inputs in place."""
+    sides = inputs.batch_sides(12, seed=inputs.SEED_BATCH + 1)
+    grids, host = _stencil_batch(sides, 7300)
+    ws = _ws(len(grids))
+    plan = binding.acs_batch_prepare(binding.KIND_STENCIL, grids, ws)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        binding.acs_batch_launch(plan, stream=s)            # warm-up outside capture
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        binding.acs_batch_launch(plan, stream=torch.cuda.current_stream())
+    for rep in range(3):
+        for q, (u_d, a_d, out) in enumerate(grids):
+            u_new = host[q][0] * (1.0 + 0.5 * rep)
+            u_d.copy_(torch.from_numpy(u_new))
+            out.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        for q, (u_d, a_d, out) in enumerate(grids):
+            u_new = host[q][0] * (1.0 + 0.5 * rep)
+            assert_parity(out.cpu().numpy(), oracle.stencil(u_new, host[q][1]), what=f"replay {rep} grid {q}")
+
+
+def test_batch_workspace_errors():
+    grids, _ = _stencil_batch([(8, 8, 8), (9, 9, 9)], 7400)
+    small = torch.zeros(4, dtype=torch.float64, device="cuda")
+    with pytest.raises(binding.AcsError) as ei:
+        binding.acs_batch_prepare(binding.KIND_STENCIL, grids, small)
+    assert ei.value.name == "ACS_ERR_WORKSPACE"
+    ws = _ws(2)
+    mis = ws.view(torch.uint8)[8:]
+    with pytest.raises(binding.AcsError) as ei:
+        binding.acs_batch_prepare(binding.KIND_STENCIL, grids, mis)
+    assert ei.value.name == "ACS_ERR_ALIGN"
+    with pytest.raises(binding.AcsError) as ei:
+        binding.acs_batch_prepare(binding.KIND_STENCIL, grids, ws, tile=(48, 8, 8))
+    assert ei.value.name == "ACS_ERR_UNSUPPORTED"
+
+
+def test_autotune_single_grid_and_cache_roundtrip(tmp_path):
+    binding.acs_tune_cache_clear()
+    u, a = inputs.stencil_fields(64, 48, 40, seed=7500)
+    ud, ad = to_dev(u), to_dev(a)
+    out = torch.empty((40, 48, 64), dtype=torch.float64, device="cuda")
+    tile, ms = binding.acs_autotune_stencil(ud, ad, out)
+    assert tile[0] in (16, 32, 64) and tile[1] in (4, 8, 16) and tile[2] >= 1 and ms > 0
+    U = inputs.rhs_field(40, 36, 30, halo=2, seed=7501)
+    Ud = to_dev(U)
+    R = torch.empty((5, 30, 36, 40), dtype=torch.float64, device="cuda")
+    rtile, rms = binding.acs_autotune_rhs(Ud, R)
+    assert rtile[0] in (16, 32, 64) and rms > 0
+    assert binding.acs_tune_cache_size() == 2
+    # a NULL-tile call now runs with the tuned shape; results still match the oracle
+    out.fill_(float("nan"))
+    binding.acs_stencil_saturated(ud, ad, out)
+    R.fill_(float("nan"))
+    binding.acs_rhs_saturated(Ud, R)
+    torch.cuda.synchronize()
+    assert_parity(out.cpu().numpy(), oracle.stencil(u, a), what="tuned stencil")
+    assert_parity(R.cpu().numpy(), oracle.rhs(U), what="tuned rhs")
+    path = str(tmp_path / "tune.txt")
+    binding.acs_tune_cache_save(path)
+    binding.acs_tune_cache_clear()
+    assert binding.acs_tune_cache_size() == 0
+    binding.acs_tune_cache_load(path)
+    assert binding.acs_tune_cache_size() == 2
+    with open(path) as f:
+        assert f.readline().startswith("acs-tune-cache 1")
+    bad = tmp_path / "bad.txt"
+    bad.write_text("acs-tune-cache 1\n48 8 8 1.0 1:8x8x8;\n")
+    with pytest.raises(binding.AcsError):
+        binding.acs_tune_cache_load(str(bad))
+    binding.acs_tune_cache_clear()
+
+
+def test_autotune_batch_picks_a_working_tile():
+    sides = inputs.batch_sides(16, seed=inputs.SEED_BATCH + 2)
+    grids, host = _stencil_batch(sides, 7600)
+    ws = _ws(len(grids))
+    tile, ms = binding.acs_autotune_batch(binding.KIND_STENCIL, grids, ws)
+    assert ms > 0
+    plan = binding.acs_batch_prepare(binding.KIND_STENCIL, grids, ws, tile=tile)
+    for (_, _, out) in grids:
+        out.fill_(float("nan"))
+    binding.acs_batch_launch(plan)
+    torch.cuda.synchronize()
+    for (u, a), (_, _, out) in zip(host, grids):
+        assert_parity(out.cpu().numpy(), oracle.stencil(u, a), what=f"tuned batch {u.shape}")
+    binding.acs_tune_cache_clear()

@@ -205,3 +205,39 @@ def test_gpu_call_reports_invalid_tile():
         binding.acs_rhs_saturated(U, R, tile=(24, 8, 0))
     assert ei.value.name == "ACS_ERR_UNSUPPORTED"
     assert torch.all(R == 0)
+
+
+# ------------------------------------------------------------------- ablation ladder
+
+LADDER = ["cse", "cse_sat", "cse_bulk", "accsat"]
+
+
+@pytest.mark.parametrize("form", LADDER)
+@pytest.mark.parametrize("dims", [(1, 1, 1), (37, 29, 23), (64, 16, 9)])
+def test_rhs_ladder_forms_ragged(form, dims):
+    nx, ny, nz = dims
+    U = inputs.rhs_field(nx, ny, nz, halo=2, seed=5000 + nx)
+    ref = oracle.rhs(U, h=(1.0, 0.5, 2.0))
+    Ud = to_dev(U)
+    R = torch.full((5, nz, ny, nx), float("nan"), dtype=torch.float64, device="cuda")
+    binding.acs_rhs_form(Ud, R, form, h=(1.0, 0.5, 2.0))
+    torch.cuda.synchronize()
+    assert_parity(R.cpu().numpy(), ref, what=f"rhs {form} {dims}")
+
+
+@pytest.mark.parametrize("form", LADDER + ["as_written", "saturated"])
+def test_rhs_ladder_forms_128cubed(form):
+    U = inputs.rhs_field(128, halo=2, seed=inputs.SEED_RHS_LARGE)
+    ref = oracle.rhs(U, threads=8)
+    Ud = to_dev(U)
+    R = torch.full((5, 128, 128, 128), float("nan"), dtype=torch.float64, device="cuda")
+    binding.acs_rhs_form(Ud, R, form)
+    torch.cuda.synchronize()
+    assert_parity(R.cpu().numpy(), ref, what=f"rhs {form} 128^3")
+
+
+def test_rhs_form_rejects_unknown_form():
+    U = to_dev(inputs.rhs_field(4, halo=2, seed=1))
+    R = torch.zeros((5, 4, 4, 4), dtype=torch.float64, device="cuda")
+    with pytest.raises(binding.AcsError):
+        binding.acs_rhs_form(U, R, 9)
