@@ -209,6 +209,24 @@ acs_status acs_batch_prepare(const acs_batch_item *items, int n, int kind, const
 /* acs_batch_launch - run a prepared batch; `params` as given for its kind above. */
 acs_status acs_batch_launch(const acs_batch_plan *plan, const void *params, acs_stream stream);
 
+/*
+ * acs_batch_run_static - a batch (as acs_batch_prepare + acs_batch_launch) that allocates
+ * nothing and takes no workspace. The paper has no counterpart; it serves callers that
+ * cannot call cudaMalloc when they run a batch: applications that give this library a fixed
+ * device budget through their own allocator, or time-critical loops that cannot accept the
+ * synchronisation an allocation may cause. The scratch (work counter and unit table) lives
+ * in a fixed device array inside the library, sized for ACS_BATCH_STATIC_MAX grids, held on
+ * every GPU that loads the library until the process exits. n > ACS_BATCH_STATIC_MAX
+ * returns ACS_ERR_WORKSPACE without launching. The first call on a device looks up the
+ * array's device address with that device current; make that first call before any stream
+ * capture. Every call uploads the unit table (synchronising `stream`, as acs_batch_prepare
+ * does), zeroes the counter and launches; calls share the array, so calls whose work
+ * overlaps on the GPU race. `tile` NULL = 32 x 8, z-chunks of 16; `params` as for the kind.
+ */
+#define ACS_BATCH_STATIC_MAX 256
+acs_status acs_batch_run_static(const acs_batch_item *items, int n, int kind, const acs_tile *tile,
+                                const void *params, acs_stream stream);
+
 /* ---------------------------------------------------------------------------------------
  * Launch-shape autotuner. Each call times every built tile with several z-chunk lengths on
  * the caller's buffers (outputs are overwritten, `stream` is synchronised: do not capture),

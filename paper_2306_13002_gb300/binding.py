@@ -62,7 +62,8 @@ _lib = None
 FORMS = {"as_written": 0, "cse": 1, "cse_sat": 2, "cse_bulk": 3, "accsat": 4, "saturated": 5}
 
 EXPORTS = ("acs_rhs_plain", "acs_rhs_saturated", "acs_rhs_form", "acs_stencil_plain", "acs_stencil_saturated",
-           "acs_batch_workspace_bytes", "acs_batch_prepare", "acs_batch_launch", "acs_autotune_rhs",
+           "acs_batch_workspace_bytes", "acs_batch_prepare", "acs_batch_launch", "acs_batch_run_static",
+           "acs_autotune_rhs",
            "acs_autotune_stencil", "acs_autotune_batch", "acs_tune_cache_save", "acs_tune_cache_load",
            "acs_tune_cache_clear", "acs_tune_cache_size", "acs_status_string", "acs_last_error", "acs_abi_version")
 
@@ -95,6 +96,7 @@ def lib() -> ctypes.CDLL:
             L.acs_batch_prepare.argtypes = [ctypes.POINTER(BatchItem), st, st, T, p, ctypes.c_size_t,
                                             ctypes.POINTER(BatchPlan), p]
             L.acs_batch_launch.argtypes = [ctypes.POINTER(BatchPlan), p, p]
+            L.acs_batch_run_static.argtypes = [ctypes.POINTER(BatchItem), st, st, T, p, p]
             L.acs_autotune_rhs.argtypes = [p, p, G, ctypes.POINTER(RhsParams), T, f32p, p]
             L.acs_autotune_stencil.argtypes = [p, p, p, G, ctypes.POINTER(ctypes.c_double), T, f32p, p]
             L.acs_autotune_batch.argtypes = [ctypes.POINTER(BatchItem), st, st, p, p, ctypes.c_size_t, T, f32p, p]
@@ -102,7 +104,7 @@ def lib() -> ctypes.CDLL:
             L.acs_tune_cache_load.argtypes = [ctypes.c_char_p]
             L.acs_tune_cache_clear.restype = None
             L.acs_tune_cache_size.restype = st
-            for f in ("acs_batch_prepare", "acs_batch_launch", "acs_autotune_rhs", "acs_autotune_stencil",
+            for f in ("acs_batch_prepare", "acs_batch_launch", "acs_batch_run_static", "acs_autotune_rhs", "acs_autotune_stencil",
                       "acs_autotune_batch", "acs_tune_cache_save", "acs_tune_cache_load"):
                 getattr(L, f).restype = st
             L.acs_status_string.argtypes = [st]
@@ -266,6 +268,25 @@ def acs_batch_prepare(kind: int, grids, ws, tile=None, halo: int | None = None, 
 def acs_batch_launch(plan: BatchPlan, params=None, stream=None) -> None:
     ptr, keep = _batch_params(plan.kind, params)
     _check(lib().acs_batch_launch(ctypes.byref(plan), ptr, _stream_ptr(stream)), "acs_batch_launch")
+    del keep
+
+
+BATCH_STATIC_MAX = 256
+
+
+def acs_batch_run_static(kind: int, grids, params=None, tile=None, halo: int | None = None, stream=None) -> None:
+    """Run a batch with the library's fixed device scratch: no workspace, no allocation.
+
+    For callers that cannot allocate device memory when they run a batch (a fixed budget
+    handed out by their own allocator, or a loop that cannot accept an allocation's
+    synchronisation). At most BATCH_STATIC_MAX grids; calls share the scratch, so calls
+    that overlap on the GPU race. The first call on a device sets up the scratch address;
+    make it before any stream capture.
+    """
+    items = batch_items(kind, grids, halo)
+    ptr, keep = _batch_params(kind, params)
+    _check(lib().acs_batch_run_static(items, len(grids), kind, _tile(tile), ptr, _stream_ptr(stream)),
+           "acs_batch_run_static")
     del keep
 
 

@@ -342,6 +342,25 @@ acs_status acs_batch_launch(const acs_batch_plan* plan, const void* params, acs_
     return batch_launch(hp, rk, sc, (cudaStream_t)stream);
 }
 
+acs_status acs_batch_run_static(const acs_batch_item* items, int n, int kind, const acs_tile* tile,
+                                const void* params, acs_stream stream) {
+    std::vector<Geom> geo;
+    acs_status st = check_batch_items(items, n, kind, geo);
+    if (st != ACS_OK) return st;
+    if (n > ACS_BATCH_STATIC_MAX)
+        return fail(ACS_ERR_WORKSPACE, "%d grids exceed the static scratch maximum of %d grids", n, ACS_BATCH_STATIC_MAX);
+    acs_tile t = tile ? *tile : acs_tile{32, 8, 16, 0};
+    if (t.kchunk == 0) t.kchunk = 16;
+    if (t.flags != 0 || t.kchunk < 1) return fail(ACS_ERR_INVALID, "bad batch tile (kchunk %d, flags %d)", t.kchunk, t.flags);
+    if (!(kind == ACS_KIND_RHS ? rhs_tile_supported(t.bx, t.by) : star_tile_supported(t.bx, t.by)))
+        return fail(ACS_ERR_UNSUPPORTED, "tile %dx%d is not built", t.bx, t.by);
+    RhsConst rk;
+    StarCoef sc;
+    st = batch_params(kind, params, rk, sc);
+    if (st != ACS_OK) return st;
+    return batch_run_static(items, geo.data(), n, kind, t, rk, sc, (cudaStream_t)stream);
+}
+
 acs_status acs_autotune_rhs(const double* U, double* R, const acs_grid* g, const acs_rhs_params* p, acs_tile* best,
                             float* best_ms, acs_stream stream) {
     Geom geo;

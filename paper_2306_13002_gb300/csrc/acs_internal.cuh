@@ -110,6 +110,8 @@ size_t batch_ws_bytes(int n);
 acs_status batch_prepare_host(const acs_batch_item* items, const Geom* geo, int n, int kind, const acs_tile& tile,
                               unsigned char* ws, size_t ws_bytes, cudaStream_t s, BatchPlanHost& plan);
 acs_status batch_launch(const BatchPlanHost& p, const RhsConst& rk, const StarCoef& sc, cudaStream_t s);
+acs_status batch_run_static(const acs_batch_item* items, const Geom* geo, int n, int kind, const acs_tile& tile,
+                            const RhsConst& rk, const StarCoef& sc, cudaStream_t s);
 
 // Autotuner (tune.cu).
 bool tuned_tile(int kind, const Geom& g, acs_tile* t);
