@@ -250,11 +250,24 @@ def main() -> None:
     ap.add_argument("--no-plain", action="store_true", help="skip the as-written timing")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end timing")
     ap.add_argument("--n", type=int, default=N_RHS, help="RHS interior side (256 is the benchmark workload)")
+    ap.add_argument("--ranker", action="store_true",
+                    help="instead of the step benchmark: the rewriter-variant ranker study (512 variants at 256^3)")
+    ap.add_argument("--variants", type=int, default=512)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     args.steps = max(args.steps, 1)
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.ranker:
+        from paper_2306_13002_gb300 import build as acs_build
+        from paper_2306_13002_gb300 import ranker
+        acs_build.build()
+        t = time.time()
+        res = ranker.study(n_variants=args.variants, n_train=int(round(args.variants * 400 / 512)), n=args.n)
+        res["wall_s"] = time.time() - t
+        print(json.dumps({"study": "learned variant ranker", "metric": "chosen-variant time / measured best",
+                          "unit": "ratio", **res}))
         return
 
     import torch

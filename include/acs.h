@@ -246,6 +246,65 @@ acs_status acs_tune_cache_load(const char *path);
 void acs_tune_cache_clear(void);
 int acs_tune_cache_size(void);
 
+/* ---------------------------------------------------------------------------------------
+ * Host rewriter of the RHS body (paper Sec. IV-VI) and its learned ranker.
+ *
+ * acs_variant_generate builds the as-written body in an e-graph, saturates it with the
+ * Table I rules plus the rule families the paper leaves off (division, distributivity,
+ * subtraction/negation), drawing the families, their order and the limits (at most 10,000
+ * e-nodes, 10 iterations) from (seed, index), extracts one program under the paper's cost
+ * model (Sec. V-B) with per-variant cost factors, and emits it as a CUDA kernel (first-use
+ * or bulk-load order, Sec. VI). index 0 is the body with only hash-consing (plain CSE).
+ * Host only; no GPU is touched. `src` / `dag` may be NULL; a too-small buffer returns
+ * ACS_ERR_INVALID with the needed size in info->src_bytes / dag_bytes.
+ * The DAG text has one line "id op a b c payload" per extracted node in emission order
+ * (op in const, param, load, add, sub, mul, div, fma, neg, rcp; fma(a,b,c) = a*b + c;
+ * const payload = IEEE bits; load payload = component * 13 + point, points 0 = p,
+ * 1..6 = +x,-x,+y,-y,+z,-z, 7..12 = the same at distance 2; param 0 gamma, 1 eps,
+ * 2..4 = 1/(2h)) and a line "R c id" per output component.
+ * ------------------------------------------------------------------------------------- */
+#define ACS_VARIANT_NFEAT 16
+typedef struct acs_variant_info {
+    float feats[ACS_VARIANT_NFEAT];  /* static features; names from acs_variant_feature_name */
+    double cost;                     /* the paper's cost of the extracted DAG, shared nodes once */
+    int enodes, eclasses, iterations;
+    int block_x;                     /* threads along x of the variant's 256-thread block */
+    long long src_bytes, dag_bytes;  /* buffer sizes needed (including the terminating 0) */
+} acs_variant_info;
+
+acs_status acs_variant_generate(unsigned long long seed, int index, char *src, size_t src_len, char *dag,
+                                size_t dag_len, acs_variant_info *info);
+const char *acs_variant_feature_name(int i);
+
+/* Compile a generated variant with NVRTC for sm_103a (FMA contraction off) and load it.
+ * ACS_ERR_UNSUPPORTED if libnvrtc cannot be loaded. `regs` receives the register count. */
+typedef struct acs_variant_module *acs_variant_handle;
+acs_status acs_variant_build(const char *src, int block_x, acs_variant_handle *out, int *regs);
+/* Run a loaded variant on a grid (same geometry rules as acs_rhs_plain). */
+acs_status acs_variant_launch(acs_variant_handle h, const double *U, double *R, const acs_grid *g,
+                              const acs_rhs_params *p, acs_stream stream);
+void acs_variant_free(acs_variant_handle h);
+
+/* FP32 MLP ranker (3 layers, ReLU, hidden width `hidden`): parameters and workspace sizes. */
+size_t acs_ranker_param_count(int n_feats, int hidden);
+size_t acs_ranker_workspace_bytes(int n, int n_feats, int hidden);
+/* Train on n variants: feats (device, n x n_feats floats), times_ms (device, n floats > 0);
+ * writes the model into params (device, acs_ranker_param_count floats). Full-batch Adam on
+ * the squared error of the standardised log time; deterministic for a given seed. */
+acs_status acs_ranker_train(const float *feats, const float *times_ms, int n, int n_feats, int hidden, int epochs,
+                            float lr, unsigned long long seed, float *params, void *ws, size_t ws_bytes,
+                            acs_stream stream);
+typedef struct acs_ranker_model {
+    int n_feats;
+    int hidden;
+    const float *params;   /* device */
+} acs_ranker_model;
+/* Rank n variants, fastest first. feats: device (n x n_feats); scores_dev: device scratch of
+ * n floats; order_out / score_out: host arrays of n (score = predicted ms, or the analytical
+ * cost feats[i][0] when model is NULL). Synchronises `stream`. */
+acs_status acs_variant_rank(const float *feats, int n, int n_feats, const acs_ranker_model *model, float *scores_dev,
+                            int *order_out, float *score_out, acs_stream stream);
+
 /* Static text for a status code. */
 const char *acs_status_string(acs_status s);
 

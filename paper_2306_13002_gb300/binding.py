@@ -55,6 +55,17 @@ class BatchPlan(ctypes.Structure):
 
 
 KIND_RHS, KIND_STENCIL = 0, 1
+VARIANT_NFEAT = 16
+
+
+class VariantInfo(ctypes.Structure):
+    _fields_ = [("feats", ctypes.c_float * VARIANT_NFEAT), ("cost", ctypes.c_double), ("enodes", ctypes.c_int),
+                ("eclasses", ctypes.c_int), ("iterations", ctypes.c_int), ("block_x", ctypes.c_int),
+                ("src_bytes", ctypes.c_longlong), ("dag_bytes", ctypes.c_longlong)]
+
+
+class RankerModel(ctypes.Structure):
+    _fields_ = [("n_feats", ctypes.c_int), ("hidden", ctypes.c_int), ("params", ctypes.c_void_p)]
 
 _lock = threading.Lock()
 _lib = None
@@ -65,7 +76,10 @@ EXPORTS = ("acs_rhs_plain", "acs_rhs_saturated", "acs_rhs_form", "acs_stencil_pl
            "acs_batch_workspace_bytes", "acs_batch_prepare", "acs_batch_launch", "acs_batch_run_static",
            "acs_autotune_rhs",
            "acs_autotune_stencil", "acs_autotune_batch", "acs_tune_cache_save", "acs_tune_cache_load",
-           "acs_tune_cache_clear", "acs_tune_cache_size", "acs_status_string", "acs_last_error", "acs_abi_version")
+           "acs_tune_cache_clear", "acs_tune_cache_size", "acs_variant_generate", "acs_variant_feature_name",
+           "acs_variant_build", "acs_variant_launch", "acs_variant_free", "acs_ranker_param_count",
+           "acs_ranker_workspace_bytes", "acs_ranker_train", "acs_variant_rank", "acs_status_string",
+           "acs_last_error", "acs_abi_version")
 
 
 def lib() -> ctypes.CDLL:
@@ -106,6 +120,26 @@ def lib() -> ctypes.CDLL:
             L.acs_tune_cache_size.restype = st
             for f in ("acs_batch_prepare", "acs_batch_launch", "acs_batch_run_static", "acs_autotune_rhs", "acs_autotune_stencil",
                       "acs_autotune_batch", "acs_tune_cache_save", "acs_tune_cache_load"):
+                getattr(L, f).restype = st
+            L.acs_variant_generate.argtypes = [ctypes.c_ulonglong, st, ctypes.c_char_p, ctypes.c_size_t,
+                                               ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(VariantInfo)]
+            L.acs_variant_feature_name.argtypes = [st]
+            L.acs_variant_feature_name.restype = ctypes.c_char_p
+            L.acs_variant_build.argtypes = [ctypes.c_char_p, st, ctypes.POINTER(ctypes.c_void_p),
+                                            ctypes.POINTER(ctypes.c_int)]
+            L.acs_variant_launch.argtypes = [p, p, p, G, ctypes.POINTER(RhsParams), p]
+            L.acs_variant_free.argtypes = [p]
+            L.acs_variant_free.restype = None
+            L.acs_ranker_param_count.argtypes = [st, st]
+            L.acs_ranker_param_count.restype = ctypes.c_size_t
+            L.acs_ranker_workspace_bytes.argtypes = [st, st, st]
+            L.acs_ranker_workspace_bytes.restype = ctypes.c_size_t
+            L.acs_ranker_train.argtypes = [p, p, st, st, st, st, ctypes.c_float, ctypes.c_ulonglong, p, p,
+                                           ctypes.c_size_t, p]
+            L.acs_variant_rank.argtypes = [p, st, st, ctypes.POINTER(RankerModel), p, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_float), p]
+            for f in ("acs_variant_generate", "acs_variant_build", "acs_variant_launch", "acs_ranker_train",
+                      "acs_variant_rank"):
                 getattr(L, f).restype = st
             L.acs_status_string.argtypes = [st]
             L.acs_status_string.restype = ctypes.c_char_p
@@ -332,3 +366,78 @@ def acs_tune_cache_clear() -> None:
 
 def acs_tune_cache_size() -> int:
     return int(lib().acs_tune_cache_size())
+
+
+# ------------------------------------------------------------------ rewriter and ranker
+
+def acs_variant_feature_names() -> list[str]:
+    return [lib().acs_variant_feature_name(i).decode() for i in range(VARIANT_NFEAT)]
+
+
+def acs_variant_generate(seed: int, index: int):
+    """(cuda_source, dag_text, VariantInfo) of rewriter variant `index` (host only)."""
+    info = VariantInfo()
+    _check(lib().acs_variant_generate(int(seed), int(index), None, 0, None, 0, ctypes.byref(info)),
+           "acs_variant_generate")
+    src = ctypes.create_string_buffer(int(info.src_bytes))
+    dag = ctypes.create_string_buffer(int(info.dag_bytes))
+    _check(lib().acs_variant_generate(int(seed), int(index), src, len(src), dag, len(dag), ctypes.byref(info)),
+           "acs_variant_generate")
+    return src.value.decode(), dag.value.decode(), info
+
+
+class Variant:
+    """A compiled, loaded rewriter variant (freed with close())."""
+
+    def __init__(self, src: str, block_x: int):
+        h, regs = ctypes.c_void_p(), ctypes.c_int()
+        _check(lib().acs_variant_build(src.encode(), int(block_x), ctypes.byref(h), ctypes.byref(regs)),
+               "acs_variant_build")
+        self.handle, self.regs = h, regs.value
+
+    def launch(self, U, R, gamma=1.4, eps=0.25, h=(1.0, 1.0, 1.0), halo=2, stream=None):
+        g = grid_for(U, R, halo, 5)
+        pr = _params(gamma, eps, h)
+        _check(lib().acs_variant_launch(self.handle, U.data_ptr(), R.data_ptr(), ctypes.byref(g), ctypes.byref(pr),
+                                        _stream_ptr(stream)), "acs_variant_launch")
+
+    def close(self):
+        if self.handle:
+            lib().acs_variant_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def acs_ranker_param_count(n_feats: int, hidden: int) -> int:
+    return int(lib().acs_ranker_param_count(int(n_feats), int(hidden)))
+
+
+def acs_ranker_workspace_bytes(n: int, n_feats: int, hidden: int) -> int:
+    return int(lib().acs_ranker_workspace_bytes(int(n), int(n_feats), int(hidden)))
+
+
+def acs_ranker_train(feats, times_ms, params, ws, hidden=64, epochs=3000, lr=3e-3, seed=13006, stream=None):
+    """Train the MLP on device tensors feats (n x F float32) and times_ms (n float32)."""
+    n, F = feats.shape
+    _check(lib().acs_ranker_train(feats.data_ptr(), times_ms.data_ptr(), int(n), int(F), int(hidden), int(epochs),
+                                  float(lr), int(seed), params.data_ptr(), ws.data_ptr(),
+                                  ws.numel() * ws.element_size(), _stream_ptr(stream)), "acs_ranker_train")
+
+
+def acs_variant_rank(feats, params=None, hidden=64, scores_dev=None, stream=None):
+    """(order fastest-first, scores) for device feats; params None = the paper's analytical cost."""
+    import torch
+    n, F = feats.shape
+    if scores_dev is None:
+        scores_dev = torch.empty(n, dtype=torch.float32, device=feats.device)
+    order = (ctypes.c_int * n)()
+    score = (ctypes.c_float * n)()
+    model = RankerModel(int(F), int(hidden), params.data_ptr()) if params is not None else None
+    _check(lib().acs_variant_rank(feats.data_ptr(), int(n), int(F), ctypes.byref(model) if model else None,
+                                  scores_dev.data_ptr(), order, score, _stream_ptr(stream)), "acs_variant_rank")
+    return list(order), list(score)

@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <set>
@@ -393,6 +394,84 @@ acs_status acs_autotune_batch(const acs_batch_item* items, int n, int kind, cons
     if (st != ACS_OK) return st;
     return tune_batch(items, geo.data(), n, kind, rk, sc, (unsigned char*)ws, ws_bytes, (cudaStream_t)stream, best,
                       best_ms);
+}
+
+acs_status acs_variant_generate(unsigned long long seed, int index, char* src, size_t src_len, char* dag,
+                                size_t dag_len, acs_variant_info* info) {
+    if (index < 0) return fail(ACS_ERR_INVALID, "variant index must be >= 0");
+    try {
+        return variant_generate(seed, index, src, src_len, dag, dag_len, info);
+    } catch (...) {
+        return fail(ACS_ERR_INVALID, "variant generation failed (out of memory?)");
+    }
+}
+
+const char* acs_variant_feature_name(int i) { return variant_feature_name(i); }
+
+acs_status acs_variant_build(const char* src, int block_x, acs_variant_handle* out, int* regs) {
+    if (!src || !out) return fail(ACS_ERR_INVALID, "src or out is NULL");
+    *out = nullptr;
+    return variant_build(src, block_x, out, regs);
+}
+
+acs_status acs_variant_launch(acs_variant_handle h, const double* U, double* R, const acs_grid* g,
+                              const acs_rhs_params* p, acs_stream stream) {
+    if (!h) return fail(ACS_ERR_INVALID, "variant handle is NULL");
+    Geom geo;
+    RhsConst k;
+    acs_status st = check_rhs(U, R, g, p, geo, k);
+    if (st != ACS_OK) return st;
+    const int by = 256 / h->bx;
+    if ((geo.ny + by - 1) / by > 65535) return fail(ACS_ERR_INVALID, "ny too large for this variant's block");
+    return variant_launch(h, U, R, geo, k, (cudaStream_t)stream);
+}
+
+void acs_variant_free(acs_variant_handle h) { variant_free(h); }
+
+size_t acs_ranker_param_count(int n_feats, int hidden) { return ranker_param_count(n_feats, hidden); }
+
+size_t acs_ranker_workspace_bytes(int n, int n_feats, int hidden) { return ranker_ws_bytes(n, n_feats, hidden); }
+
+acs_status acs_ranker_train(const float* feats, const float* times_ms, int n, int n_feats, int hidden, int epochs,
+                            float lr, unsigned long long seed, float* params, void* ws, size_t ws_bytes,
+                            acs_stream stream) {
+    if (!feats || !times_ms || !params || !ws) return fail(ACS_ERR_INVALID, "NULL pointer");
+    if (n < 2 || n_feats < 1 || n_feats > 1024 || hidden < 1 || hidden > 1024 || epochs < 1 || !(lr > 0.f))
+        return fail(ACS_ERR_INVALID, "bad ranker training size or rate");
+    if (!aligned(ws, 16) || !aligned(params, 4) || !aligned(feats, 4)) return fail(ACS_ERR_ALIGN, "misaligned buffer");
+    return ranker_train(feats, times_ms, n, n_feats, hidden, epochs, lr, seed, params, ws, ws_bytes,
+                        (cudaStream_t)stream);
+}
+
+acs_status acs_variant_rank(const float* feats, int n, int n_feats, const acs_ranker_model* model, float* scores_dev,
+                            int* order_out, float* score_out, acs_stream stream) {
+    if (!feats || !scores_dev || !order_out) return fail(ACS_ERR_INVALID, "NULL pointer");
+    if (n < 1 || n_feats < 1) return fail(ACS_ERR_INVALID, "bad sizes");
+    cudaStream_t s = (cudaStream_t)stream;
+    acs_status st;
+    if (model) {
+        if (!model->params || model->n_feats != n_feats || model->hidden < 1 || model->hidden > 1024)
+            return fail(ACS_ERR_NOMODEL, "model does not match the features");
+        st = ranker_predict(feats, n, n_feats, model->hidden, model->params, scores_dev, s);
+    } else {
+        st = analytical_scores(feats, n, n_feats, scores_dev, s);
+    }
+    if (st != ACS_OK) return st;
+    std::vector<float> sc(n);
+    if (cudaMemcpyAsync(sc.data(), scores_dev, n * sizeof(float), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return launch_status("acs_variant_rank: reading scores");
+    if (model) {
+        st = ranker_denormalise(model->params, n_feats, model->hidden, sc);
+        if (st != ACS_OK) return st;
+    }
+    std::vector<int> ord(n);
+    for (int i = 0; i < n; ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return sc[a] < sc[b]; });
+    for (int i = 0; i < n; ++i) order_out[i] = ord[i];
+    if (score_out)
+        for (int i = 0; i < n; ++i) score_out[i] = sc[i];
+    return ACS_OK;
 }
 
 acs_status acs_tune_cache_save(const char* path) {

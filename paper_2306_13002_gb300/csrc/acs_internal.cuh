@@ -4,7 +4,17 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "acs.h"
+
+// A compiled rewriter variant (NVRTC cubin loaded through the runtime library API).
+struct acs_variant_module {
+    cudaLibrary_t lib;
+    cudaKernel_t kern;
+    int bx;
+    int regs;
+};
 
 namespace acs {
 
@@ -126,6 +136,22 @@ acs_status tune_cache_save(const char* path);
 acs_status tune_cache_load(const char* path);
 void tune_cache_clear();
 int tune_cache_size();
+
+// Rewriter, variants and ranker.
+acs_status variant_generate(unsigned long long seed, int index, char* src, size_t src_len, char* dag, size_t dag_len,
+                            acs_variant_info* info);
+const char* variant_feature_name(int i);
+acs_status variant_build(const char* src, int block_x, acs_variant_module** out, int* regs);
+acs_status variant_launch(acs_variant_module* m, const double* U, double* R, const Geom& g, const RhsConst& k,
+                          cudaStream_t s);
+void variant_free(acs_variant_module* m);
+size_t ranker_param_count(int F, int H);
+size_t ranker_ws_bytes(int n, int F, int H);
+acs_status ranker_train(const float* feats, const float* times, int n, int F, int H, int epochs, float lr,
+                        unsigned long long seed, float* params, void* ws, size_t ws_bytes, cudaStream_t s);
+acs_status ranker_predict(const float* feats, int n, int F, int H, const float* params, float* scores, cudaStream_t s);
+acs_status analytical_scores(const float* feats, int n, int F, float* scores, cudaStream_t s);
+acs_status ranker_denormalise(const float* params, int F, int H, std::vector<float>& y);
 
 // Shared-memory bytes and legality of a saturated tile.
 bool rhs_tile_supported(int bx, int by);

@@ -1,0 +1,138 @@
+"""Rewriter variants and the learned ranker: generation, compilation, timing, training, ranking.
+
+The pipeline the paper's extraction step stands for, with a learned cost in place of the
+fixed one: the host rewriter (`acs_variant_generate`) produces N equivalent programs of the
+RHS body from random rule orders; each is compiled with NVRTC and timed on the GPU; an FP32
+MLP (`acs_ranker_train`, hand-written CUDA kernels) learns time from static features on a
+training split; `acs_variant_rank` orders the held-out variants by the model and, for
+comparison, by the paper's analytical cost (Sec. V-B).
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import os
+
+import numpy as np
+
+from . import binding, inputs
+
+
+def spearman(a, b) -> float:
+    """Spearman rank correlation with average ranks for ties."""
+    def ranks(x):
+        x = np.asarray(x, dtype=np.float64)
+        order = np.argsort(x, kind="mergesort")
+        r = np.empty(len(x))
+        r[order] = np.arange(len(x), dtype=np.float64)
+        for v in np.unique(x):                      # average ranks of ties
+            idx = np.where(x == v)[0]
+            if len(idx) > 1:
+                r[idx] = r[idx].mean()
+        return r
+    ra, rb = ranks(a), ranks(b)
+    ra -= ra.mean()
+    rb -= rb.mean()
+    den = np.sqrt((ra * ra).sum() * (rb * rb).sum())
+    return float((ra * rb).sum() / den) if den > 0 else 0.0
+
+
+def generate(n: int, seed: int = inputs.SEED_VARIANTS):
+    """Host rewriter output for variants 0..n-1: list of dicts (src, dag, feats, cost, ...)."""
+    out = []
+    for i in range(n):
+        src, dag, info = binding.acs_variant_generate(seed, i)
+        out.append({"index": i, "src": src, "dag": dag, "feats": np.array(info.feats[:], dtype=np.float32),
+                    "cost": info.cost, "block_x": info.block_x, "enodes": info.enodes,
+                    "iterations": info.iterations})
+    return out
+
+
+def compile_all(variants, threads: int | None = None):
+    """NVRTC-compile every variant in parallel; fills v['module'] and the register feature."""
+    threads = threads or min(16, os.cpu_count() or 4)
+
+    def build(v):
+        return binding.Variant(v["src"], v["block_x"])
+
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        mods = list(ex.map(build, variants))
+    reg_idx = binding.acs_variant_feature_names().index("regs")
+    for v, m in zip(variants, mods):
+        v["module"] = m
+        v["feats"][reg_idx] = float(m.regs)
+    return variants
+
+
+def time_all(variants, U, R, reps: int = 5, stream=None):
+    """Mean CUDA-event time (ms) of each variant over `reps` launches after one warm-up."""
+    import torch
+    s = stream or torch.cuda.current_stream()
+    for v in variants:
+        m = v["module"]
+        m.launch(U, R, stream=s)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        for _ in range(reps):
+            m.launch(U, R, stream=s)
+        b.record(s)
+        b.synchronize()
+        v["ms"] = a.elapsed_time(b) / reps
+    return variants
+
+
+def study(n_variants: int = 512, n_train: int = 400, n: int = 256, seed: int = inputs.SEED_VARIANTS,
+          hidden: int = 64, epochs: int = 3000, lr: float = 3e-3, reps: int = 5) -> dict:
+    """Generate, compile and time the variants at n^3, train on n_train, evaluate on the rest."""
+    import torch
+    vs = compile_all(generate(n_variants, seed))
+    U = torch.from_numpy(inputs.rhs_field(n, halo=2, seed=inputs.SEED_RHS_LARGE)).cuda()
+    R = torch.empty((5, n, n, n), dtype=torch.float64, device="cuda")
+    time_all(vs, U, R, reps=reps)
+    # consistency of one variant's output with the library's ACCSAT form (sanity only)
+    Rc = torch.empty_like(R)
+    binding.acs_rhs_form(U, Rc, "accsat")
+    vs[1]["module"].launch(U, R)
+    torch.cuda.synchronize()
+    rel = float(((R - Rc).abs() / (1e-12 * Rc.abs() + 1e-14)).max())
+    perm = np.random.default_rng(seed).permutation(n_variants)
+    tr, te = perm[:n_train], perm[n_train:]
+    F = len(vs[0]["feats"])
+    X = torch.from_numpy(np.stack([v["feats"] for v in vs])).cuda()
+    T = torch.tensor([v["ms"] for v in vs], dtype=torch.float32, device="cuda")
+    params = torch.empty(binding.acs_ranker_param_count(F, hidden), dtype=torch.float32, device="cuda")
+    ws = torch.empty(binding.acs_ranker_workspace_bytes(n_train, F, hidden) // 4 + 4, dtype=torch.float32,
+                     device="cuda")
+    tri = torch.from_numpy(tr).cuda()
+    tei = torch.from_numpy(te).cuda()
+    Xtr, Ttr = X[tri].contiguous(), T[tri].contiguous()
+    Xte = X[tei].contiguous()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    binding.acs_ranker_train(Xtr, Ttr, params, ws, hidden=hidden, epochs=epochs, lr=lr, seed=seed)
+    t1.record()
+    torch.cuda.synchronize()
+    train_ms = t0.elapsed_time(t1)
+    order_m, pred = binding.acs_variant_rank(Xte, params, hidden)
+    order_a, cost = binding.acs_variant_rank(Xte, None)
+    times_te = np.array([vs[i]["ms"] for i in te])
+    _, pred_tr = binding.acs_variant_rank(Xtr, params, hidden)
+    times_tr = np.array([vs[i]["ms"] for i in tr])
+    best = float(times_te.min())
+    pick_m = float(times_te[order_m[0]])
+    pick_a = float(times_te[order_a[0]])
+    all_ms = np.array([v["ms"] for v in vs])
+    for v in vs:
+        v["module"].close()
+    return {
+        "variants": n_variants, "train": n_train, "test": n_variants - n_train, "grid": n,
+        "hidden": hidden, "epochs": epochs, "lr": lr, "train_ms": train_ms,
+        "spearman_mlp_test": spearman(pred, times_te),
+        "spearman_mlp_train": spearman(pred_tr, times_tr),
+        "spearman_analytical_test": spearman(cost, times_te),
+        "best_test_ms": best, "mlp_pick_ms": pick_m, "analytical_pick_ms": pick_a,
+        "mlp_pick_over_best": pick_m / best, "analytical_pick_over_best": pick_a / best,
+        "all_ms_min": float(all_ms.min()), "all_ms_median": float(np.median(all_ms)),
+        "all_ms_max": float(all_ms.max()), "variant1_vs_accsat_err_over_tol": rel,
+        "distinct_sources": len({v["src"] for v in vs}),
+    }
