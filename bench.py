@@ -179,6 +179,18 @@ def run_reference(args) -> None:
     }))
 
 
+def reduce_over_ranks(dist, x: float, op: str, device: str) -> float:
+    """Max or sum of a per-rank scalar over all ranks (identity without a process group).
+
+    Used only for timing and throughput bookkeeping: the replicas exchange no data."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def time_launches(torch, fn, steps: int, stream) -> tuple[float, float]:
     """Per-launch CUDA-event durations on `stream`; returns (mean launch ms, region ms)."""
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -239,6 +251,81 @@ def bench_batch(torch, binding, inputs, stream, steps: int) -> dict:
     return res
 
 
+def run_large(args) -> None:
+    """RHS 512^3 (as written, ACCSAT, ranker-picked variant, autotuned saturated) and the star
+    stencil at 768^3 (as written, autotuned saturated); one JSON line with fractions of the
+    FP64-pipe and HBM rooflines."""
+    import torch
+    from paper_2306_13002_gb300 import binding, inputs, ranker
+    from paper_2306_13002_gb300 import build as acs_build
+    acs_build.build()
+    stream = torch.cuda.current_stream()
+    steps = max(3, min(args.steps, 10))
+    peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    out = {"study": "large workloads", "unit": UNIT}
+    # ranker-picked variant: a 128-variant study at 256^3, then the pick is timed at 512^3
+    small = ranker.study(n_variants=128, n_train=100, n=256, epochs=2000, reps=3)
+    n = 512
+    U = torch.from_numpy(inputs.rhs_field(n, halo=2, seed=inputs.SEED_HUGE)).cuda()
+    R = torch.empty((5, n, n, n), dtype=torch.float64, device="cuda")
+    pts = n ** 3
+    algo_bytes = (U.numel() + R.numel()) * 8
+    rhs = {"grid": [n] * 3, "in_gb": U.numel() * 8 / 1e9, "out_gb": R.numel() * 8 / 1e9}
+    tile, _ = binding.acs_autotune_rhs(U, R)
+    for form, fn in (("as_written", lambda: binding.acs_rhs_form(U, R, "as_written")),
+                     ("accsat", lambda: binding.acs_rhs_form(U, R, "accsat")),
+                     ("saturated_autotuned", lambda: binding.acs_rhs_saturated(U, R, tile=tile))):
+        fn()
+        torch.cuda.synchronize()
+        _, rm = time_launches(torch, fn, steps, stream)
+        ms = rm / steps
+        rhs[form] = {"ms": ms, "gpts": pts / (ms * 1e-3) / 1e9}
+    # the variants the learned ranker and the analytical cost picked at 256^3, timed at 512^3
+    for name, key in (("mlp_pick_variant", "mlp_pick_index"), ("analytical_pick_variant", "analytical_pick_index")):
+        src, _, info = binding.acs_variant_generate(inputs.SEED_VARIANTS, small[key])
+        m = binding.Variant(src, info.block_x)
+        fn = lambda: m.launch(U, R)  # noqa: E731
+        fn()
+        torch.cuda.synchronize()
+        _, rm = time_launches(torch, fn, steps, stream)
+        rhs[name] = {"ms": rm / steps, "gpts": pts / (rm / steps * 1e-3) / 1e9, "index": small[key]}
+        m.close()
+    sat = rhs["saturated_autotuned"]["ms"]
+    rhs["tile"] = list(tile)
+    rhs["fp64_frac"] = DP_OPS_PER_POINT["rhs_saturated"] * pts / (sat * 1e-3) / 1e9 / DP_PEAK_GOPS
+    rhs["hbm_frac"] = algo_bytes / (sat * 1e-3) / 1e9 / hbm
+    rhs["speedup_saturated_over_as_written"] = rhs["as_written"]["ms"] / sat
+    out["rhs_512"] = rhs
+    out["ranker_study_256"] = {k: small[k] for k in ("spearman_mlp_test", "spearman_analytical_test",
+                                                    "mlp_pick_over_best", "analytical_pick_over_best")}
+    del U, R
+    torch.cuda.empty_cache()
+    n = 768
+    u_np, a_np = inputs.stencil_fields(n, halo=4, seed=inputs.SEED_HUGE)
+    u, a = torch.from_numpy(u_np).cuda(), torch.from_numpy(a_np).cuda()
+    del u_np, a_np
+    o = torch.empty((n, n, n), dtype=torch.float64, device="cuda")
+    pts = n ** 3
+    algo_bytes = (u.numel() + a.numel() + o.numel()) * 8
+    st = {"grid": [n] * 3}
+    tile, _ = binding.acs_autotune_stencil(u, a, o)
+    for form, fn in (("as_written", lambda: binding.acs_stencil_plain(u, a, o)),
+                     ("saturated_autotuned", lambda: binding.acs_stencil_saturated(u, a, o, tile=tile))):
+        fn()
+        torch.cuda.synchronize()
+        _, rm = time_launches(torch, fn, steps, stream)
+        ms = rm / steps
+        st[form] = {"ms": ms, "gpts": pts / (ms * 1e-3) / 1e9}
+    sat = st["saturated_autotuned"]["ms"]
+    st["tile"] = list(tile)
+    st["fp64_frac"] = DP_OPS_PER_POINT["star_saturated"] * pts / (sat * 1e-3) / 1e9 / DP_PEAK_GOPS
+    st["hbm_frac"] = algo_bytes / (sat * 1e-3) / 1e9 / hbm
+    st["speedup_saturated_over_as_written"] = st["as_written"]["ms"] / sat
+    out["stencil_768"] = st
+    print(json.dumps(out))
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -253,11 +340,16 @@ def main() -> None:
     ap.add_argument("--ranker", action="store_true",
                     help="instead of the step benchmark: the rewriter-variant ranker study (512 variants at 256^3)")
     ap.add_argument("--variants", type=int, default=512)
+    ap.add_argument("--large", action="store_true",
+                    help="instead of the step benchmark: RHS 512^3 and star stencil 768^3, all forms")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     args.steps = max(args.steps, 1)
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.large:
+        run_large(args)
         return
     if args.ranker:
         from paper_2306_13002_gb300 import build as acs_build
@@ -293,18 +385,10 @@ def main() -> None:
             dist.barrier()
 
     def max_over_ranks(x: float) -> float:
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_over_ranks(dist, x, "max", "cuda")
 
     def sum_over_ranks(x: float) -> float:
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+        return reduce_over_ranks(dist, x, "sum", "cuda")
 
     n = args.n
     U_host = inputs.rhs_field(n, halo=2, seed=inputs.SEED_RHS_LARGE + rank)

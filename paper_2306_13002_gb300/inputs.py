@@ -46,15 +46,27 @@ def splitmix64(seed: int, counters: np.ndarray) -> np.ndarray:
 
 
 def uniform(seed: int, start: int, count: int, lo: float, hi: float, out: np.ndarray | None = None) -> np.ndarray:
-    """Uniform doubles in [lo, hi) for counters start .. start+count-1 (chunked, bounded memory)."""
+    """Uniform doubles in [lo, hi) for counters start .. start+count-1 (chunked, bounded memory;
+    large requests are split across threads, which changes no value)."""
     if out is None:
         out = np.empty(count, dtype=np.float64)
     scale = float(hi) - float(lo)
-    for s in range(0, count, _CHUNK):
+
+    def chunk(s):
         n = min(_CHUNK, count - s)
         z = splitmix64(seed, np.arange(start + s, start + s + n, dtype=np.uint64))
         u = (z >> np.uint64(11)).astype(np.float64) * TWO_M53
         out[s:s + n] = lo + scale * u
+
+    starts = range(0, count, _CHUNK)
+    if count > 4 * _CHUNK:
+        import concurrent.futures as cf
+        import os
+        with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+            list(ex.map(chunk, starts))
+    else:
+        for s in starts:
+            chunk(s)
     return out
 
 

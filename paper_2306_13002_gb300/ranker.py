@@ -135,4 +135,6 @@ def study(n_variants: int = 512, n_train: int = 400, n: int = 256, seed: int = i
         "all_ms_min": float(all_ms.min()), "all_ms_median": float(np.median(all_ms)),
         "all_ms_max": float(all_ms.max()), "variant1_vs_accsat_err_over_tol": rel,
         "distinct_sources": len({v["src"] for v in vs}),
+        "mlp_pick_index": int(te[order_m[0]]), "analytical_pick_index": int(te[order_a[0]]),
+        "best_test_index": int(te[int(np.argmin(times_te))]),
     }
