@@ -48,9 +48,9 @@ DP_PEAK_GOPS = 2 * SMS * SM_MAX_MHZ / 1000.0
 # DRAM bytes per launch measured by ncu for the current kernel source (keyed by the SHA-256 of
 # the files that define it); a changed kernel reports null until it is profiled again.
 NCU_TRAFFIC = {
-    # ncu --set full of rhs_saturated_kernel<32,8> at 192^3 (564 MB DRAM read+write), scaled by
+    # ncu --set full of rhs_saturated_kernel<32,8> at 192^3 (564.1 MB DRAM read+write), scaled by
     # points to one 256^3 launch; summary in profiles/rhs_saturated_192cubed_ncu_full.md.
-    "31af6eec0a8e26b3": 1336558175,
+    "5eba2c473232f04f": 1337200000,
 }
 
 
