@@ -50,13 +50,13 @@ DP_PEAK_GOPS = 2 * SMS * SM_MAX_MHZ / 1000.0
 NCU_TRAFFIC = {
     # ncu --set full of rhs_saturated_kernel<32,8> at 192^3 (564.1 MB DRAM read+write), scaled by
     # points to one 256^3 launch; summary in profiles/rhs_saturated_192cubed_ncu_full.md.
-    "5eba2c473232f04f": 1337200000,
+    "9967afc167d72b7e": 1337200000,
 }
 
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("march.cuh", "rhs_saturated.cu", "acs_internal.cuh"):
+    for f in ("march.cuh", "rhs_saturated.cu", "device_ops.cuh"):
         with open(os.path.join(ROOT, "paper_2306_13002_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -205,6 +205,28 @@ def time_launches(torch, fn, steps: int, stream) -> tuple[float, float]:
     torch.cuda.synchronize()
     per = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     return sum(per) / len(per), r0.elapsed_time(r1)
+
+
+def bench_block(torch, binding, inputs, stream, steps: int) -> dict:
+    """The block-assembly body (75 statements, 151 loads per point) at 128^3, four forms."""
+    n = 128
+    A, B, G = inputs.block_fields(n, halo=1, seed=inputs.SEED_BLOCK)
+    Ad, Bd, Gd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), torch.from_numpy(G).cuda()
+    del A, B, G
+    out = torch.empty((75, n, n, n), dtype=torch.float64, device="cuda")
+    res = {"grid": [n] * 3, "bytes_per_point_algorithmic": 8 * (51 + 75)}
+    for form in ("as_written", "cse", "cse_bulk", "saturated"):
+        fn = lambda f=form: binding.acs_block_form(Ad, Bd, Gd, out, f, stream=stream)  # noqa: E731
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        _, rm = time_launches(torch, fn, steps, stream)
+        ms = rm / steps
+        res[form] = {"ms": ms, "gpts": n ** 3 / (ms * 1e-3) / 1e9,
+                     "hbm_gbs_algorithmic": 8 * (51 + 75) * n ** 3 / (ms * 1e-3) / 1e9}
+    del Ad, Bd, Gd, out
+    torch.cuda.empty_cache()
+    return res
 
 
 def bench_batch(torch, binding, inputs, stream, steps: int) -> dict:
@@ -564,6 +586,8 @@ def main() -> None:
         "parity": parity,
         "stencil_384": stencil,
     }
+    if not args.no_stencil:
+        result["block_128"] = bench_block(torch, binding, inputs, stream, max(3, min(args.steps, 20)))
     if not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(U_host)
     print(json.dumps(result))

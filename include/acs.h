@@ -305,6 +305,22 @@ typedef struct acs_ranker_model {
 acs_status acs_variant_rank(const float *feats, int n, int n_feats, const acs_ranker_model *model, float *scores_dev,
                             int *order_out, float *score_out, acs_stream stream);
 
+/*
+ * acs_block_form - the block-assembly body (a third loop body, the many-statement shape of
+ * the paper's Listing 2): per interior point 75 outputs from 5 x 5 blocks A, B on the planes
+ * k-1, k, k+1 and a scalar G, with t1 = dt q1, t2 = dt q2 and q = 5m + n:
+ *   out[q]      = -t2 A_q(k-1) - t1 B_q(k-1) - t1 q3 G [m = n]
+ *   out[25 + q] = 2 t1 B_q(k) - q4 t2 A_q(k) + [m = n] (1 + 2 t1 q3 G)
+ *   out[50 + q] = t2 A_q(k+1) - t1 B_q(k+1) - t1 q3 G [m = n]
+ *   A, B   25 components each (stride g->in_sc), halo >= 1; G one component with the same
+ *          row/plane strides; out 75 components (stride g->out_sc)
+ *   prm    5 host doubles {dt, q1, q2, q3, q4}
+ *   form   ACS_FORM_AS_WRITTEN, ACS_FORM_CSE, ACS_FORM_CSE_BULK or ACS_FORM_SATURATED
+ *          (constants folded, every operation an FMA, loads free to move ahead of stores)
+ */
+acs_status acs_block_form(const double *A, const double *B, const double *G, double *out, const acs_grid *g,
+                          const double *prm, int form, acs_stream stream);
+
 /* Static text for a status code. */
 const char *acs_status_string(acs_status s);
 

@@ -72,6 +72,8 @@ class Oracle:
         lib.oracle_rhs.restype = None
         lib.oracle_stencil.argtypes = [p, p, p, i32, i32, i32, i32, i64, i64, i64, i64, p, i32, i32, i32]
         lib.oracle_stencil.restype = None
+        lib.oracle_block.argtypes = [p, p, p, p, i32, i32, i32, i32, i64, i64, i64, i64, i64, i64, p, i32, i32, i32]
+        lib.oracle_block.restype = None
         lib.oracle_has_openmp.restype = i32
         self.lib = lib
 
@@ -117,6 +119,26 @@ class Oracle:
         return out
 
 
+    def block(self, A: np.ndarray, B: np.ndarray, G: np.ndarray, prm=(0.01, 1.5, 2.0, 0.75, 0.5), halo: int = 1,
+              k_range: tuple[int, int] | None = None, threads: int = 1) -> np.ndarray:
+        """Block-assembly body. A, B: (25, Z, Y, X); G: (Z, Y, X) with the same strides per component.
+        Returns out: (75, nz, ny, nx)."""
+        if A.shape != B.shape or A.ndim != 4 or A.shape[0] != 25 or G.shape != A.shape[1:]:
+            raise ValueError("A, B must be (25, Z, Y, X) and G (Z, Y, X)")
+        if halo < 1:
+            raise ValueError("the block body needs a halo of at least 1")
+        sc, sz, sy, _ = _strides(A)
+        if _strides(B) != (sc, sz, sy, 1) or _strides(G) != (sz, sy, 1):
+            raise ValueError("A, B and G must share strides")
+        nz, ny, nx = (s - 2 * halo for s in A.shape[1:])
+        out = np.full((75, nz, ny, nx), np.nan)
+        k0, k1 = (0, nz) if k_range is None else k_range
+        pr = np.ascontiguousarray(prm, dtype=np.float64)
+        self.lib.oracle_block(A.ctypes.data, B.ctypes.data, G.ctypes.data, out.ctypes.data, nx, ny, nz, halo, sy, sz,
+                              sc, nx, nx * ny, nx * ny * nz, pr.ctypes.data, int(k0), int(k1), int(threads))
+        return out
+
+
 def default() -> Oracle:
     global _lib
     with _lock:
@@ -147,6 +169,11 @@ def has_openmp() -> bool:
 def rhs(U, gamma=1.4, eps=0.25, h=(1.0, 1.0, 1.0), halo=2, k_range=None, threads=1):
     """As-written RHS through the default oracle build (see `Oracle.rhs`)."""
     return default().rhs(U, gamma, eps, h, halo, k_range, threads)
+
+
+def block(A, B, G, prm=(0.01, 1.5, 2.0, 0.75, 0.5), halo=1, k_range=None, threads=1):
+    """Block-assembly body through the default oracle build (see `Oracle.block`)."""
+    return default().block(A, B, G, prm, halo, k_range, threads)
 
 
 def stencil(u, a, c=None, halo=4, k_range=None, threads=1):

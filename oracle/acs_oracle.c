@@ -23,6 +23,7 @@
  *  2. Variable-coefficient 25-point star stencil (the halo Jacobi shape of SPEC ostencil,
  *     Table III, widened to radius 4):
  *         out(p) = sum_{d=x,y,z} sum_{o=1..4} c_{d,o} a(p) (u(p+o e_d) - 2u(p) + u(p-o e_d))
+ *  3. A block-assembly body with many statements (see oracle_block below).
  *
  * Layout: x fastest. Inputs are halo-extended arrays addressed from their corner cell,
  * element (i, j, k) of component c at c*isc + k*isz + j*isy + i; interior point (i, j, k)
@@ -140,4 +141,54 @@ int oracle_has_openmp(void)
 #else
     return 0;
 #endif
+}
+
+/*
+ * 3. Block-assembly body (the many-statement shape of the paper's Listing 2: tens of
+ *    stores, each an affine combination of a few loads, with loop-invariant temporaries).
+ *    Synthetic coefficients. Inputs: A[25], B[25] (5 x 5 blocks, component q = 5m + n) and a
+ *    scalar field G, all halo-extended; at interior p with k-neighbours p-, p+ (along z):
+ *      t1 = dt * q1, t2 = dt * q2
+ *      L_q = -t2 * A_q(p-) - t1 * B_q(p-) - t1 * q3 * G(p) * [m == n]
+ *      D_q = 2 * t1 * B_q(p) - q4 * t2 * A_q(p) + [m == n] * (1 + 2 * t1 * q3 * G(p))
+ *      W_q = t2 * A_q(p+) - t1 * B_q(p+) - t1 * q3 * G(p) * [m == n]
+ *    Output component o = 25 s + q for s = 0 (L), 1 (D), 2 (W): 75 outputs per point.
+ *    prm = {dt, q1, q2, q3, q4}.
+ */
+void oracle_block(const double *A, const double *B, const double *G, double *out, int nx, int ny, int nz,
+                  int halo, i64 isy, i64 isz, i64 isc, i64 osy, i64 osz, i64 osc, const double *prm,
+                  int k0, int k1, int nthreads)
+{
+    int k;
+    if (k0 < 0)
+        k0 = 0;
+    if (k1 > nz)
+        k1 = nz;
+    (void)nthreads;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+    for (k = k0; k < k1; ++k) {
+        for (int j = 0; j < ny; ++j) {
+            for (int i = 0; i < nx; ++i) {
+                const i64 p = (i64)(k + halo) * isz + (i64)(j + halo) * isy + (i64)(i + halo);
+                const i64 o = (i64)k * osz + (i64)j * osy + i;
+                const double dt = prm[0], q1 = prm[1], q2 = prm[2], q3 = prm[3], q4 = prm[4];
+                for (int m = 0; m < 5; ++m) {
+                    for (int n = 0; n < 5; ++n) {
+                        const int q = 5 * m + n;
+                        const double t1 = dt * q1;
+                        const double t2 = dt * q2;
+                        const double diag = (m == n) ? 1.0 : 0.0;
+                        out[(i64)q * osc + o] = -t2 * A[(i64)q * isc + p - isz] - t1 * B[(i64)q * isc + p - isz]
+                                                - t1 * q3 * G[p] * diag;
+                        out[(i64)(25 + q) * osc + o] = 2.0 * t1 * B[(i64)q * isc + p] - q4 * t2 * A[(i64)q * isc + p]
+                                                       + diag * (1.0 + 2.0 * t1 * q3 * G[p]);
+                        out[(i64)(50 + q) * osc + o] = t2 * A[(i64)q * isc + p + isz] - t1 * B[(i64)q * isc + p + isz]
+                                                       - t1 * q3 * G[p] * diag;
+                    }
+                }
+            }
+        }
+    }
 }

@@ -79,7 +79,7 @@ EXPORTS = ("acs_rhs_plain", "acs_rhs_saturated", "acs_rhs_form", "acs_stencil_pl
            "acs_tune_cache_clear", "acs_tune_cache_size", "acs_variant_generate", "acs_variant_feature_name",
            "acs_variant_build", "acs_variant_launch", "acs_variant_free", "acs_ranker_param_count",
            "acs_ranker_workspace_bytes", "acs_ranker_train", "acs_variant_rank", "acs_status_string",
-           "acs_last_error", "acs_abi_version")
+           "acs_last_error", "acs_abi_version", "acs_block_form")
 
 
 def lib() -> ctypes.CDLL:
@@ -141,6 +141,8 @@ def lib() -> ctypes.CDLL:
             for f in ("acs_variant_generate", "acs_variant_build", "acs_variant_launch", "acs_ranker_train",
                       "acs_variant_rank"):
                 getattr(L, f).restype = st
+            L.acs_block_form.argtypes = [p, p, p, p, G, ctypes.POINTER(ctypes.c_double), st, p]
+            L.acs_block_form.restype = st
             L.acs_status_string.argtypes = [st]
             L.acs_status_string.restype = ctypes.c_char_p
             L.acs_last_error.restype = ctypes.c_char_p
@@ -441,3 +443,23 @@ def acs_variant_rank(feats, params=None, hidden=64, scores_dev=None, stream=None
     _check(lib().acs_variant_rank(feats.data_ptr(), int(n), int(F), ctypes.byref(model) if model else None,
                                   scores_dev.data_ptr(), order, score, _stream_ptr(stream)), "acs_variant_rank")
     return list(order), list(score)
+
+
+BLOCK_PRM = (0.01, 1.5, 2.0, 0.75, 0.5)
+
+
+def acs_block_form(A, B, G, out, form, prm=BLOCK_PRM, halo: int = 1, stream=None) -> None:
+    """Block-assembly body; A, B (25, Z, Y, X), G (Z, Y, X), out (75, nz, ny, nx) device tensors."""
+    f = FORMS[form] if isinstance(form, str) else int(form)
+    _, Z, Y, X = A.shape
+    isc, isz, isy, isx = A.stride()
+    if tuple(B.stride()) != (isc, isz, isy, isx) or tuple(G.stride()) != (isz, isy, isx) or isx != 1:
+        raise ValueError("A, B and G must share strides (x unit stride)")
+    osc, osz, osy, osx = out.stride()
+    nx, ny, nz = X - 2 * halo, Y - 2 * halo, Z - 2 * halo
+    if tuple(out.shape) != (75, nz, ny, nx) or osx != 1:
+        raise ValueError("out must be (75, nz, ny, nx) with unit x stride")
+    g = Grid(nx, ny, nz, halo, isy, isz, isc, osy, osz, osc)
+    pr = (ctypes.c_double * 5)(*[float(v) for v in prm])
+    _check(lib().acs_block_form(A.data_ptr(), B.data_ptr(), G.data_ptr(), out.data_ptr(), ctypes.byref(g), pr, f,
+                                _stream_ptr(stream)), "acs_block_form")

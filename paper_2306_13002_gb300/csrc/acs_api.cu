@@ -280,6 +280,28 @@ acs_status acs_rhs_form(const double* U, double* R, const acs_grid* g, const acs
     return launch_rhs_ladder(U, R, geo, k, form, (cudaStream_t)stream);
 }
 
+acs_status acs_block_form(const double* A, const double* B, const double* G, double* out, const acs_grid* g,
+                          const double* prm, int form, acs_stream stream) {
+    if (!A || !B || !G || !out) return fail(ACS_ERR_INVALID, "A, B, G or out is NULL");
+    if (!prm) return fail(ACS_ERR_INVALID, "parameters are NULL");
+    if (!aligned(A, 8) || !aligned(B, 8) || !aligned(G, 8) || !aligned(out, 8))
+        return fail(ACS_ERR_ALIGN, "arrays must be 8-byte aligned");
+    if (form != ACS_FORM_AS_WRITTEN && form != ACS_FORM_CSE && form != ACS_FORM_CSE_BULK && form != ACS_FORM_SATURATED)
+        return fail(ACS_ERR_INVALID, "block body form %d is not built", form);
+    Geom geo;
+    acs_status st = check_grid(g, 1, 2, geo);
+    if (st != ACS_OK) return st;
+    const i64 Z = (i64)geo.nz + 2 * geo.halo;
+    if (g->in_sc < g->in_sz * Z) return fail(ACS_ERR_INVALID, "in_sc too small for A/B");
+    if (g->out_sc < g->out_sz * geo.nz) return fail(ACS_ERR_INVALID, "out_sc too small");
+    for (int q = 0; q < 5; ++q)
+        if (!std::isfinite(prm[q])) return fail(ACS_ERR_INVALID, "parameter %d is not finite", q);
+    const Span so = span_of(out, 75, geo.osc, geo.nz, geo.osz, geo.ny, geo.osy, geo.nx);
+    if (overlap(in_span(A, geo, 25), so) || overlap(in_span(B, geo, 25), so) || overlap(in_span(G, geo, 1), so))
+        return fail(ACS_ERR_ALIAS, "out overlaps an input");
+    return launch_block(A, B, G, out, geo, prm, form, (cudaStream_t)stream);
+}
+
 acs_status acs_stencil_plain(const double* u, const double* a, double* out, const acs_grid* g, const double* c,
                              acs_stream stream) {
     Geom geo;

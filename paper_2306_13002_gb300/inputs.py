@@ -99,6 +99,23 @@ def stencil_fields(nx: int, ny: int | None = None, nz: int | None = None, halo: 
     return u, a
 
 
+SEED_BLOCK = 13008          # block-assembly body
+
+
+def block_fields(nx: int, ny: int | None = None, nz: int | None = None, halo: int = 1,
+                 seed: int = SEED_BLOCK) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """(A, B, G) for the block-assembly body: A, B (25, Z, Y, X) uniform in [-1, 1), G (Z, Y, X)
+    uniform in [0.5, 1.5); counters A: 0.., B: 25V.., G: 50V.. (V = extended volume)."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    shape = (nz + 2 * halo, ny + 2 * halo, nx + 2 * halo)
+    vol = shape[0] * shape[1] * shape[2]
+    A = uniform(seed, 0, 25 * vol, -1.0, 1.0).reshape((25,) + shape)
+    B = uniform(seed, 25 * vol, 25 * vol, -1.0, 1.0).reshape((25,) + shape)
+    G = uniform(seed, 50 * vol, vol, 0.5, 1.5).reshape(shape)
+    return A, B, G
+
+
 def batch_sides(n_grids: int, seed: int = SEED_BATCH, lo: int = 16, hi: int = 160) -> np.ndarray:
     """Grid sides (n_grids, 3) as (nx, ny, nz), each round(exp(U(ln lo, ln hi))) clamped to [lo, hi].
 

@@ -241,3 +241,36 @@ def test_rhs_form_rejects_unknown_form():
     R = torch.zeros((5, 4, 4, 4), dtype=torch.float64, device="cuda")
     with pytest.raises(binding.AcsError):
         binding.acs_rhs_form(U, R, 9)
+
+
+# --------------------------------------------------------------- block-assembly body
+
+BLOCK_FORMS = ["as_written", "cse", "cse_bulk", "saturated"]
+
+
+@pytest.mark.parametrize("form", BLOCK_FORMS)
+@pytest.mark.parametrize("dims", [(1, 1, 1), (37, 5, 9), (130, 3, 70)])
+def test_block_forms_match_oracle(form, dims):
+    nx, ny, nz = dims
+    A, B, G = inputs.block_fields(nx, ny, nz, halo=1, seed=6000 + nx)
+    prm = (0.013, 1.7, 2.3, 0.61, 0.37)
+    ref = oracle.block(A, B, G, prm=prm)
+    out = torch.full((75, nz, ny, nx), float("nan"), dtype=torch.float64, device="cuda")
+    binding.acs_block_form(to_dev(A), to_dev(B), to_dev(G), out, form, prm=prm)
+    torch.cuda.synchronize()
+    assert_parity(out.cpu().numpy(), ref, what=f"block {form} {dims}")
+
+
+@pytest.mark.parametrize("form", BLOCK_FORMS)
+def test_block_forms_halo2_padded(form):
+    nx, ny, nz, h = 21, 6, 11, 2
+    A, B, G = inputs.block_fields(nx, ny, nz, halo=h, seed=6100)
+    ref = oracle.block(A, B, G, halo=h)
+    Ad, Bd = padded_dev(A, A.shape[-1] + 3), padded_dev(B, B.shape[-1] + 3)
+    Gd = padded_dev(G, G.shape[-1] + 3)
+    big = torch.full((75, nz + 1, ny, nx + 2), float("nan"), dtype=torch.float64, device="cuda")
+    out = big[:, 1:, :, 1:1 + nx]
+    binding.acs_block_form(Ad, Bd, Gd, out, form, halo=h)
+    torch.cuda.synchronize()
+    assert_parity(out.cpu().numpy(), ref, what=f"block {form} padded")
+    assert torch.isnan(big[:, 0]).all() and torch.isnan(big[:, :, :, 0]).all()

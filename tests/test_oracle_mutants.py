@@ -6,6 +6,7 @@ the pin battery of `test_oracle_pins` runs against it and at least one pin must 
 import pytest
 
 import oracle
+import test_oracle_block as blk
 import test_oracle_pins as pins
 
 MUTANTS = [
@@ -30,6 +31,11 @@ MUTANTS = [
     ("stencil weights reversed", "c[4 * d + (o - 1)]", "c[4 * d + (4 - o)]"),
     ("stencil coefficient field off by one", "* a[p] *", "* a[p + 1] *"),
     ("stencil minus side at o-1", "+ u[p - s]);", "+ u[p - s + stride[d]]);"),
+    ("block: lower block reads the upper plane", "-t2 * A[(i64)q * isc + p - isz]", "-t2 * A[(i64)q * isc + p + isz]"),
+    ("block: diagonal G term on every entry", "const double diag = (m == n) ? 1.0 : 0.0;",
+     "const double diag = 1.0;"),
+    ("block: outputs of L and W swapped", "out[(i64)(50 + q) * osc + o] = t2", "out[(i64)q * osc + o + 0 * osc] = t2"),
+    ("block: D uses 2 t2 B", "= 2.0 * t1 * B[(i64)q * isc + p]", "= 2.0 * t2 * B[(i64)q * isc + p]"),
 ]
 
 
@@ -49,7 +55,11 @@ def _battery(orc):
         (pins.test_stencil_polynomials_exact_to_degree_9, {"d": 1}),
         (pins.test_stencil_single_term_matches_library_correlation, {"d": 1, "o": 3}),
         (pins.test_stencil_full_weights_match_library_correlation, {}),
-    ] + [(pins.test_one_dimensional_flow_closed_form, {"d": d}) for d in range(3)]
+    ] + [(pins.test_one_dimensional_flow_closed_form, {"d": d}) for d in range(3)] + [
+        (blk.test_block_closed_form_exact_on_integers, {}),
+        (blk.test_block_zero_blocks_give_identity_structure, {}),
+        (blk.test_block_general_params_within_rounding, {}),
+    ]
     failed = []
     for fn, kw in checks:
         try:
