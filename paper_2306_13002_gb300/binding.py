@@ -79,7 +79,8 @@ EXPORTS = ("acs_rhs_plain", "acs_rhs_saturated", "acs_rhs_form", "acs_stencil_pl
            "acs_tune_cache_clear", "acs_tune_cache_size", "acs_variant_generate", "acs_variant_feature_name",
            "acs_variant_build", "acs_variant_launch", "acs_variant_free", "acs_ranker_param_count",
            "acs_ranker_workspace_bytes", "acs_ranker_train", "acs_variant_rank", "acs_status_string",
-           "acs_last_error", "acs_abi_version", "acs_block_form")
+           "acs_last_error", "acs_abi_version", "acs_block_form", "acs_rhs_host_workspace_bytes",
+           "acs_rhs_saturated_host")
 
 
 def lib() -> ctypes.CDLL:
@@ -143,6 +144,10 @@ def lib() -> ctypes.CDLL:
                 getattr(L, f).restype = st
             L.acs_block_form.argtypes = [p, p, p, p, G, ctypes.POINTER(ctypes.c_double), st, p]
             L.acs_block_form.restype = st
+            L.acs_rhs_host_workspace_bytes.argtypes = [G, st]
+            L.acs_rhs_host_workspace_bytes.restype = ctypes.c_size_t
+            L.acs_rhs_saturated_host.argtypes = [p, p, G, ctypes.POINTER(RhsParams), T, st, p, ctypes.c_size_t, p]
+            L.acs_rhs_saturated_host.restype = st
             L.acs_status_string.argtypes = [st]
             L.acs_status_string.restype = ctypes.c_char_p
             L.acs_last_error.restype = ctypes.c_char_p
@@ -463,3 +468,18 @@ def acs_block_form(A, B, G, out, form, prm=BLOCK_PRM, halo: int = 1, stream=None
     pr = (ctypes.c_double * 5)(*[float(v) for v in prm])
     _check(lib().acs_block_form(A.data_ptr(), B.data_ptr(), G.data_ptr(), out.data_ptr(), ctypes.byref(g), pr, f,
                                 _stream_ptr(stream)), "acs_block_form")
+
+
+def acs_rhs_host_workspace_bytes(U_host, R_host, halo: int = 2, slab: int = 0) -> int:
+    g = grid_for(U_host, R_host, halo, 5)
+    return int(lib().acs_rhs_host_workspace_bytes(ctypes.byref(g), int(slab)))
+
+
+def acs_rhs_saturated_host(U_host, R_host, ws, gamma=1.4, eps=0.25, h=(1.0, 1.0, 1.0), halo=2, tile=None, slab=0,
+                           stream=None) -> None:
+    """Saturated RHS on host (CPU, ideally pinned) tensors, streamed in z-slabs through `ws` (device)."""
+    g = grid_for(U_host, R_host, halo, 5)
+    pr = _params(gamma, eps, h)
+    _check(lib().acs_rhs_saturated_host(U_host.data_ptr(), R_host.data_ptr(), ctypes.byref(g), ctypes.byref(pr),
+                                        _tile(tile), int(slab), ws.data_ptr(), ws.numel() * ws.element_size(),
+                                        _stream_ptr(stream)), "acs_rhs_saturated_host")

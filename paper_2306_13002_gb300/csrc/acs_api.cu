@@ -268,6 +268,32 @@ acs_status acs_rhs_saturated(const double* U, double* R, const acs_grid* g, cons
     return launch_rhs_saturated(U, R, geo, k, t, (cudaStream_t)stream);
 }
 
+size_t acs_rhs_host_workspace_bytes(const acs_grid* g, int slab) {
+    Geom geo;
+    if (slab <= 0) slab = 32;
+    if (check_grid(g, 2, 5, geo) != ACS_OK) return 0;
+    return rhs_host_ws_bytes(geo, slab < geo.nz ? slab : geo.nz);
+}
+
+acs_status acs_rhs_saturated_host(const double* U, double* R, const acs_grid* g, const acs_rhs_params* p,
+                                  const acs_tile* tile, int slab, void* ws, size_t ws_bytes, acs_stream stream) {
+    Geom geo;
+    RhsConst k;
+    acs_status st = check_rhs(U, R, g, p, geo, k);
+    if (st != ACS_OK) return st;
+    if (slab < 0) return fail(ACS_ERR_INVALID, "slab must be >= 0");
+    if (slab == 0) slab = 32;
+    if (slab > geo.nz) slab = geo.nz;
+    acs_tile t;
+    st = check_tile(tile, kDefaultRhsTile, rhs_tile_supported, t);
+    if (st != ACS_OK) return st;
+    if (!ws) return fail(ACS_ERR_WORKSPACE, "workspace is NULL");
+    if (!aligned(ws, 16)) return fail(ACS_ERR_ALIGN, "workspace must be 16-byte aligned");
+    if (ws_bytes < rhs_host_ws_bytes(geo, slab))
+        return fail(ACS_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, rhs_host_ws_bytes(geo, slab));
+    return rhs_host_run(U, R, geo, k, t, slab, static_cast<double*>(ws), (cudaStream_t)stream);
+}
+
 acs_status acs_rhs_form(const double* U, double* R, const acs_grid* g, const acs_rhs_params* p, int form,
                         const acs_tile* tile, acs_stream stream) {
     if (form == ACS_FORM_AS_WRITTEN) return acs_rhs_plain(U, R, g, p, stream);

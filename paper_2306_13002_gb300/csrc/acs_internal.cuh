@@ -33,6 +33,9 @@ acs_status launch_rhs_plain(const double* U, double* R, const Geom& g, const Rhs
 acs_status launch_rhs_saturated(const double* U, double* R, const Geom& g, const RhsConst& k,
                                 const acs_tile& t, cudaStream_t s);
 acs_status launch_rhs_ladder(const double* U, double* R, const Geom& g, const RhsConst& k, int form, cudaStream_t s);
+size_t rhs_host_ws_bytes(const Geom& g, int slab);
+acs_status rhs_host_run(const double* U, double* R, const Geom& g, const RhsConst& k, const acs_tile& t, int slab,
+                        double* ws, cudaStream_t comp);
 acs_status launch_block(const double* A, const double* B, const double* G, double* out, const Geom& g,
                         const double* prm, int form, cudaStream_t s);
 acs_status launch_stencil_plain(const double* u, const double* a, double* out, const Geom& g,
