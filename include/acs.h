@@ -137,7 +137,7 @@ acs_status acs_rhs_saturated(const double *U, double *R, const acs_grid *g, cons
 
 /*
  * acs_rhs_saturated_host - the saturated RHS on HOST arrays, streamed through the GPU in
- * z-slabs of `slab` planes (0 = 32) so that uploads, kernels and downloads overlap.
+ * z-slabs of `slab` planes (0 = 16) so that uploads, kernels and downloads overlap.
  *   U, R   host arrays in compact layout (in_sy = nx + 2 halo, in_sz = in_sy (ny + 2 halo),
  *          out_sy = nx, out_sz = nx ny; component strides free). Page-locked memory is
  *          needed for the copies to overlap; pageable memory works but serialises.
@@ -146,7 +146,7 @@ acs_status acs_rhs_saturated(const double *U, double *R, const acs_grid *g, cons
  * Uploads and downloads run on two library-owned streams per device; `stream` runs the kernels
  * and, on return, is ordered after the last download (so a later cudaStreamSynchronize(stream)
  * means R is complete on the host). Each input plane crosses the host link once (the halo
- * planes shared by consecutive slabs are copied device to device).
+ * planes shared by consecutive slabs are copied on the device).
  */
 size_t acs_rhs_host_workspace_bytes(const acs_grid *g, int slab);
 acs_status acs_rhs_saturated_host(const double *U, double *R, const acs_grid *g, const acs_rhs_params *p,

@@ -62,8 +62,8 @@ int num_sms() {
     return cached[dev];
 }
 
-// z-chunk per block: balance whole waves of blocks against the per-chunk warm-up (one
-// extra plane of fluxes and the prologue loads, counted as ~1.5 planes of work).
+// z-chunk per block: balance whole waves of blocks against the per-chunk warm-up (one extra
+// plane of own-point fluxes plus the prologue loads, measured at ~0.35 of a plane step).
 int default_kchunk(int nz, i64 columns, int ctas_per_sm) {
     const double slots = (double)num_sms() * (ctas_per_sm > 0 ? ctas_per_sm : 1);
     static const int cand[] = {4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128};
@@ -73,7 +73,7 @@ int default_kchunk(int nz, i64 columns, int ctas_per_sm) {
         if (kc > nz && kc != cand[0]) break;
         const i64 chunks = (nz + kc - 1) / kc;
         const double waves = std::ceil((double)(columns * chunks) / slots);
-        const double cost = waves * ((kc < nz ? kc : nz) + 1.5);
+        const double cost = waves * ((kc < nz ? kc : nz) + 0.35);
         if (cost < best_cost - 1e-9) {
             best_cost = cost;
             best = kc < nz ? kc : nz;
@@ -270,7 +270,7 @@ acs_status acs_rhs_saturated(const double* U, double* R, const acs_grid* g, cons
 
 size_t acs_rhs_host_workspace_bytes(const acs_grid* g, int slab) {
     Geom geo;
-    if (slab <= 0) slab = 32;
+    if (slab <= 0) slab = 16;
     if (check_grid(g, 2, 5, geo) != ACS_OK) return 0;
     return rhs_host_ws_bytes(geo, slab < geo.nz ? slab : geo.nz);
 }
@@ -282,7 +282,7 @@ acs_status acs_rhs_saturated_host(const double* U, double* R, const acs_grid* g,
     acs_status st = check_rhs(U, R, g, p, geo, k);
     if (st != ACS_OK) return st;
     if (slab < 0) return fail(ACS_ERR_INVALID, "slab must be >= 0");
-    if (slab == 0) slab = 32;
+    if (slab == 0) slab = 16;
     if (slab > geo.nz) slab = geo.nz;
     acs_tile t;
     st = check_tile(tile, kDefaultRhsTile, rhs_tile_supported, t);

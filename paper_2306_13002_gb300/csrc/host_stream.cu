@@ -1,18 +1,22 @@
 // acs_rhs_saturated_host: the saturated RHS on host buffers, streamed through the GPU in
-// z-slabs so that host-to-device copies, the kernel and device-to-host copies overlap.
+// z-slabs so that host-to-device copies, kernels and device-to-host copies overlap.
 //
 // The grid is cut into slabs of `slab` interior z-planes. Slab s needs input planes
-// [k0-2, k1+2) and produces output planes [k0, k1). Two device input buffers and two output
-// buffers (in the caller's workspace) alternate between slabs. For slab s > 0 the four halo
-// planes it shares with slab s-1 are copied device to device from the previous input buffer,
-// so every input plane crosses the host link once. Three streams:
-//   h2d     uploads slab s (one cudaMemcpyAsync per component and plane range),
-//   caller  runs the kernel of slab s after the upload (event), and
-//   d2h     downloads slab s after its kernel (event).
-// A buffer is refilled only after the kernel (input) or the download (output) that used it
-// two slabs earlier has finished (events). The call returns once everything is enqueued; the
-// caller's stream waits for the last download, so work ordered after the call on `stream`
-// sees the finished R. Host buffers should be page-locked for the copies to overlap.
+// [k0-2, k1+2) and produces output planes [k0, k1). NB input and NB output buffers (in the
+// caller's workspace) rotate between slabs. For slab s > 0 the four halo planes it shares with
+// slab s-1 are copied from the previous input buffer by a small kernel on the upload stream,
+// so every input plane crosses the host link once (copy-engine device-to-device copies in this
+// place serialised the two link directions on GB300 and nearly doubled the step time).
+// Library-owned streams per device:
+//   up        uploads slab s (one strided cudaMemcpy2DAsync over the five components),
+//   comp[2]   run the kernel of slab s on comp[s % 2], so the tail of one slab's kernel
+//             overlaps the start of the next,
+//   down      downloads slab s after its kernel (one cudaMemcpy2DAsync).
+// Events order the hand-offs: kernel s after upload s; upload s (reusing buffer s % NB)
+// after kernel s - NB; kernel s (reusing output buffer s % NB) after download s - NB; download
+// s after kernel s. The first upload waits for everything already enqueued on the caller's
+// stream, and the caller's stream waits for the last download, so the call behaves like one
+// operation on `stream`. Host buffers should be page-locked for the copies to overlap.
 #include <mutex>
 
 #include "acs_internal.cuh"
@@ -20,8 +24,19 @@
 namespace acs {
 namespace {
 
+constexpr int NB = 3;
+
+// Copies the 2H shared halo planes of every component from the previous slab's buffer.
+__global__ void halo_planes_kernel(double* __restrict__ dst, const double* __restrict__ src, long long n_per_comp,
+                                   long long comp_stride) {
+    const int c = blockIdx.y;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_per_comp;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[c * comp_stride + i] = src[c * comp_stride + i];
+}
+
 struct StreamSet {
-    cudaStream_t h2d = nullptr, d2h = nullptr;
+    cudaStream_t up = nullptr, down = nullptr, comp[2] = {nullptr, nullptr};
     bool ok = false;
 };
 std::mutex g_ss_mu;
@@ -34,8 +49,10 @@ acs_status streams_for_device(StreamSet** out) {
     std::lock_guard<std::mutex> lk(g_ss_mu);
     StreamSet& s = g_ss[dev];
     if (!s.ok) {
-        if (cudaStreamCreateWithFlags(&s.h2d, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaStreamCreateWithFlags(&s.d2h, cudaStreamNonBlocking) != cudaSuccess)
+        if (cudaStreamCreateWithFlags(&s.up, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&s.down, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&s.comp[0], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&s.comp[1], cudaStreamNonBlocking) != cudaSuccess)
             return launch_status("cudaStreamCreateWithFlags");
         s.ok = true;
     }
@@ -44,7 +61,8 @@ acs_status streams_for_device(StreamSet** out) {
 }
 
 struct Events {
-    cudaEvent_t e[8] = {nullptr};
+    static constexpr int N = 3 * NB + 2;
+    cudaEvent_t e[N] = {nullptr};
     ~Events() {
         for (auto& x : e)
             if (x) cudaEventDestroy(x);
@@ -54,6 +72,11 @@ struct Events {
             if (cudaEventCreateWithFlags(&x, cudaEventDisableTiming) != cudaSuccess) return false;
         return true;
     }
+    cudaEvent_t up(int b) { return e[b]; }
+    cudaEvent_t done(int b) { return e[NB + b]; }
+    cudaEvent_t down(int b) { return e[2 * NB + b]; }
+    cudaEvent_t entry() { return e[3 * NB]; }
+    cudaEvent_t exit() { return e[3 * NB + 1]; }
 };
 
 }  // namespace
@@ -63,11 +86,11 @@ size_t rhs_host_ws_bytes(const Geom& g, int slab) {
     const size_t in_plane = X * Y, out_plane = (size_t)g.nx * g.ny;
     const size_t in_buf = 5 * in_plane * (size_t)(slab + 2 * g.halo);
     const size_t out_buf = 5 * out_plane * (size_t)slab;
-    return sizeof(double) * 2 * (in_buf + out_buf);
+    return sizeof(double) * NB * (in_buf + out_buf);
 }
 
 acs_status rhs_host_run(const double* U, double* R, const Geom& g, const RhsConst& k, const acs_tile& t, int slab,
-                        double* ws, cudaStream_t comp) {
+                        double* ws, cudaStream_t caller) {
     StreamSet* ss = nullptr;
     acs_status st = streams_for_device(&ss);
     if (st != ACS_OK) return st;
@@ -75,63 +98,88 @@ acs_status rhs_host_run(const double* U, double* R, const Geom& g, const RhsCons
     const i64 X = (i64)g.nx + 2 * H, Y = (i64)g.ny + 2 * H;
     const i64 in_plane = X * Y, out_plane = (i64)g.nx * g.ny;
     const i64 in_comp = in_plane * (slab + 2 * H), out_comp = out_plane * slab;
-    double* inb[2] = {ws, ws + 5 * in_comp};
-    double* outb[2] = {ws + 10 * in_comp, ws + 10 * in_comp + 5 * out_comp};
-    // The host arrays must be the compact layouts the strides describe.
     if (g.isy != X || g.isz != in_plane || g.osy != g.nx || g.osz != out_plane)
         return fail(ACS_ERR_INVALID, "host buffers must be compact (row and plane strides without padding)");
-    Events ev_up, ev_done, ev_down;  // per buffer parity: upload done, kernel done, download done
-    if (!ev_up.init() || !ev_done.init() || !ev_down.init()) return launch_status("cudaEventCreate");
+    double* inb[NB];
+    double* outb[NB];
+    for (int b = 0; b < NB; ++b) {
+        inb[b] = ws + (i64)b * 5 * in_comp;
+        outb[b] = ws + (i64)NB * 5 * in_comp + (i64)b * 5 * out_comp;
+    }
+    Events ev;
+    if (!ev.init()) return launch_status("cudaEventCreate");
+    auto chk = [](cudaError_t e, const char* what) { return e == cudaSuccess ? ACS_OK : launch_status(what); };
+    if ((st = chk(cudaEventRecord(ev.entry(), caller), "cudaEventRecord")) != ACS_OK) return st;
+    if ((st = chk(cudaStreamWaitEvent(ss->up, ev.entry(), 0), "cudaStreamWaitEvent")) != ACS_OK) return st;
     const int nslab = (g.nz + slab - 1) / slab;
-    const size_t b = sizeof(double);
+    const size_t b8 = sizeof(double);
+    // one strided copy per direction and slab while the pitches fit the 2D copy's limit
+    int max_pitch = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&max_pitch, cudaDevAttrMaxPitch, dev) != cudaSuccess) max_pitch = 0;
+    const bool use2d = (double)b8 * (double)g.isc <= (double)max_pitch && (double)b8 * (double)g.osc <= (double)max_pitch &&
+                       (double)b8 * (double)in_comp <= (double)max_pitch;
     for (int s = 0; s < nslab; ++s) {
-        const int p = s & 1;
+        const int b = s % NB, bp = (s + NB - 1) % NB;
         const int k0 = s * slab, k1 = (k0 + slab < g.nz) ? k0 + slab : g.nz, kz = k1 - k0;
-        // 1. upload: planes [k0-H, k1+H) of every component into inb[p]; for s > 0 the first
-        //    2H planes come from the previous buffer (device to device).
-        if (s >= 2 && cudaStreamWaitEvent(ss->h2d, ev_done.e[p], 0) != cudaSuccess)
-            return launch_status("cudaStreamWaitEvent");
-        for (int c = 0; c < 5; ++c) {
-            double* dst = inb[p] + (i64)c * in_comp;
-            const double* src = U + (i64)c * g.isc;   // extended plane e = k + H
-            int first = 0;                           // first extended plane index to upload, relative to k0
-            if (s > 0) {
-                const double* prev = inb[p ^ 1] + (i64)c * in_comp + (i64)slab * in_plane;  // planes [k0-H, k0+H)
-                if (cudaMemcpyAsync(dst, prev, b * 2 * H * in_plane, cudaMemcpyDeviceToDevice, ss->h2d) != cudaSuccess)
-                    return launch_status("cudaMemcpyAsync(halo planes)");
-                first = 2 * H;
-            }
-            const i64 nplanes = kz + 2 * H - first;
-            if (cudaMemcpyAsync(dst + (i64)first * in_plane, src + (i64)(k0 + first) * in_plane, b * nplanes * in_plane,
-                                cudaMemcpyHostToDevice, ss->h2d) != cudaSuccess)
-                return launch_status("cudaMemcpyAsync(host to device)");
+        cudaStream_t comp = ss->comp[s & 1];
+        // 1. upload planes [k0-H, k1+H) of every component into inb[b]
+        if (s >= NB && (st = chk(cudaStreamWaitEvent(ss->up, ev.done(b), 0), "cudaStreamWaitEvent")) != ACS_OK)
+            return st;
+        int first = 0;
+        if (s > 0) {   // the 2H planes shared with slab s-1 come from its buffer
+            halo_planes_kernel<<<dim3(64, 5), 256, 0, ss->up>>>(inb[b], inb[bp] + (i64)slab * in_plane,
+                                                                 2 * H * in_plane, in_comp);
+            if ((st = launch_status("halo_planes_kernel")) != ACS_OK) return st;
+            first = 2 * H;
         }
-        if (cudaEventRecord(ev_up.e[p], ss->h2d) != cudaSuccess) return launch_status("cudaEventRecord");
-        // 2. compute slab s on the caller's stream
-        if (cudaStreamWaitEvent(comp, ev_up.e[p], 0) != cudaSuccess) return launch_status("cudaStreamWaitEvent");
-        if (s >= 2 && cudaStreamWaitEvent(comp, ev_down.e[p], 0) != cudaSuccess)
-            return launch_status("cudaStreamWaitEvent");
+        const size_t up_bytes = b8 * (size_t)(kz + 2 * H - first) * in_plane;
+        if (use2d) {
+            if ((st = chk(cudaMemcpy2DAsync(inb[b] + (i64)first * in_plane, b8 * in_comp,
+                                            U + (i64)(k0 + first) * in_plane, b8 * g.isc, up_bytes, 5,
+                                            cudaMemcpyHostToDevice, ss->up),
+                          "cudaMemcpy2DAsync(host to device)")) != ACS_OK)
+                return st;
+        } else {
+            for (int c = 0; c < 5; ++c)
+                if ((st = chk(cudaMemcpyAsync(inb[b] + (i64)c * in_comp + (i64)first * in_plane,
+                                              U + (i64)c * g.isc + (i64)(k0 + first) * in_plane, up_bytes,
+                                              cudaMemcpyHostToDevice, ss->up),
+                              "cudaMemcpyAsync(host to device)")) != ACS_OK)
+                    return st;
+        }
+        if ((st = chk(cudaEventRecord(ev.up(b), ss->up), "cudaEventRecord")) != ACS_OK) return st;
+        // 2. kernel of slab s
+        if ((st = chk(cudaStreamWaitEvent(comp, ev.up(b), 0), "cudaStreamWaitEvent")) != ACS_OK) return st;
+        if (s >= NB && (st = chk(cudaStreamWaitEvent(comp, ev.down(b), 0), "cudaStreamWaitEvent")) != ACS_OK)
+            return st;
         Geom sg = g;
         sg.nz = kz;
         sg.isc = in_comp;
         sg.osc = out_comp;
-        st = launch_rhs_saturated(inb[p], outb[p], sg, k, t, comp);
-        if (st != ACS_OK) return st;
-        if (cudaEventRecord(ev_done.e[p], comp) != cudaSuccess) return launch_status("cudaEventRecord");
+        if ((st = launch_rhs_saturated(inb[b], outb[b], sg, k, t, comp)) != ACS_OK) return st;
+        if ((st = chk(cudaEventRecord(ev.done(b), comp), "cudaEventRecord")) != ACS_OK) return st;
         // 3. download slab s
-        if (cudaStreamWaitEvent(ss->d2h, ev_done.e[p], 0) != cudaSuccess) return launch_status("cudaStreamWaitEvent");
-        for (int c = 0; c < 5; ++c) {
-            if (cudaMemcpyAsync(R + (i64)c * g.osc + (i64)k0 * out_plane, outb[p] + (i64)c * out_comp,
-                                b * (size_t)kz * out_plane, cudaMemcpyDeviceToHost, ss->d2h) != cudaSuccess)
-                return launch_status("cudaMemcpyAsync(device to host)");
+        if ((st = chk(cudaStreamWaitEvent(ss->down, ev.done(b), 0), "cudaStreamWaitEvent")) != ACS_OK) return st;
+        const size_t down_bytes = b8 * (size_t)kz * out_plane;
+        if (use2d) {
+            if ((st = chk(cudaMemcpy2DAsync(R + (i64)k0 * out_plane, b8 * g.osc, outb[b], b8 * out_comp, down_bytes, 5,
+                                            cudaMemcpyDeviceToHost, ss->down),
+                          "cudaMemcpy2DAsync(device to host)")) != ACS_OK)
+                return st;
+        } else {
+            for (int c = 0; c < 5; ++c)
+                if ((st = chk(cudaMemcpyAsync(R + (i64)c * g.osc + (i64)k0 * out_plane, outb[b] + (i64)c * out_comp,
+                                              down_bytes, cudaMemcpyDeviceToHost, ss->down),
+                              "cudaMemcpyAsync(device to host)")) != ACS_OK)
+                    return st;
         }
-        if (cudaEventRecord(ev_down.e[p], ss->d2h) != cudaSuccess) return launch_status("cudaEventRecord");
+        if ((st = chk(cudaEventRecord(ev.down(b), ss->down), "cudaEventRecord")) != ACS_OK) return st;
     }
-    // the caller's stream waits for the last downloads (both parities)
-    for (int p = 0; p < 2 && p < nslab; ++p)
-        if (cudaStreamWaitEvent(comp, ev_down.e[(nslab - 1 - p) & 1], 0) != cudaSuccess)
-            return launch_status("cudaStreamWaitEvent");
-    return ACS_OK;
+    // the caller's stream continues after the last download (downloads are in order on `down`)
+    if ((st = chk(cudaEventRecord(ev.exit(), ss->down), "cudaEventRecord")) != ACS_OK) return st;
+    return chk(cudaStreamWaitEvent(caller, ev.exit(), 0), "cudaStreamWaitEvent");
 }
 
 }  // namespace acs
