@@ -48,9 +48,10 @@ DP_PEAK_GOPS = 2 * SMS * SM_MAX_MHZ / 1000.0
 # DRAM bytes per launch measured by ncu for the current kernel source (keyed by the SHA-256 of
 # the files that define it); a changed kernel reports null until it is profiled again.
 NCU_TRAFFIC = {
-    # ncu --set full of rhs_saturated_kernel<32,8> at 192^3 (564.1 MB DRAM read+write), scaled by
-    # points to one 256^3 launch; summary in profiles/rhs_saturated_192cubed_ncu_full.md.
-    "9967afc167d72b7e": 1337200000,
+    # one-pass ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the timed launch
+    # itself: rhs_saturated_kernel<32,8>, z-chunk 16, 256^3 (717.35 + 632.97 MB); summary in
+    # profiles/bench_256_launch_list.md.
+    "9967afc167d72b7e": 1350320000,
 }
 
 
@@ -120,23 +121,22 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(U: np.ndarray, budget_s: float = 12.0) -> dict:
+def cpu_baseline(U: np.ndarray, budget_s: float = 10.0) -> dict:
     """The oracle (as-written FP64 loop nest, gcc) on a bounded z-slab sample of the same field."""
     import oracle
     threads = os.cpu_count() or 1
     if not oracle.has_openmp():
         threads = 1
     n = U.shape[-1] - 4
-    t = time.perf_counter()
-    oracle.rhs(U, k_range=(0, 1), threads=threads)
-    t1 = max(time.perf_counter() - t, 1e-4)
-    planes = int(max(1, min(n, budget_s / t1)))
-    t = time.perf_counter()
-    oracle.rhs(U, k_range=(0, planes), threads=threads)
-    dt = time.perf_counter() - t
-    pts = planes * n * n
+    passes, pts, dt = 0, 0, 0.0
+    while dt < budget_s and passes < 200:      # whole-field passes until ~budget_s of wall time
+        t = time.perf_counter()
+        oracle.rhs(U, threads=threads)
+        dt += time.perf_counter() - t
+        pts += n ** 3
+        passes += 1
     return {"value": pts / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"as-written RHS oracle on {planes} of {n} z-planes of the {n}^3 field ({pts} points, {dt:.1f} s)"}
+            "sample": f"as-written RHS oracle, {passes} passes over the whole {n}^3 field ({pts} points, {dt:.1f} s)"}
 
 
 def run_reference(args) -> None:
@@ -362,6 +362,7 @@ def main() -> None:
     ap.add_argument("--ranker", action="store_true",
                     help="instead of the step benchmark: the rewriter-variant ranker study (512 variants at 256^3)")
     ap.add_argument("--variants", type=int, default=512)
+    ap.add_argument("--tile", default="", help="bx,by,kchunk: use this launch shape instead of the autotuner")
     ap.add_argument("--large", action="store_true",
                     help="instead of the step benchmark: RHS 512^3 and star stencil 768^3, all forms")
     args = ap.parse_args()
@@ -428,7 +429,11 @@ def main() -> None:
 
     # Launch shape from the library's autotuner (outside the timed region); tile=None calls
     # then use the tuned shape from the cache.
-    tuned_tile, tuned_ms = binding.acs_autotune_rhs(U, R, stream=stream)
+    if args.tile:
+        tuned_tile = tuple(int(v) for v in args.tile.split(","))
+        sat = lambda: binding.acs_rhs_saturated(U, R, tile=tuned_tile, stream=stream)  # noqa: E731
+    else:
+        tuned_tile, _ = binding.acs_autotune_rhs(U, R, stream=stream)
     for _ in range(args.warmup):
         sat()
     torch.cuda.synchronize()
@@ -582,7 +587,7 @@ def main() -> None:
         "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": f"rhs_saturated_{n}^3_fp64", "grid": [n] * 3, "halo": 2, "gamma": 1.4, "eps": 0.25,
-                   "tile": f"{tuned_tile[0]}x{tuned_tile[1]}, z-chunk {tuned_tile[2]} (acs_autotune_rhs)", "l2": f"inputs larger than L2 ({in_bytes / 1e6:.0f} MB in, {out_bytes / 1e6:.0f} MB out)",
+                   "tile": f"{tuned_tile[0]}x{tuned_tile[1]}, z-chunk {tuned_tile[2]}" + ("" if args.tile else " (acs_autotune_rhs)"), "l2": f"inputs larger than L2 ({in_bytes / 1e6:.0f} MB in, {out_bytes / 1e6:.0f} MB out)",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "alu", "achieved": achieved_ops, "peak": DP_PEAK_GOPS, "unit": "G FP64-pipe op/s",
                      "frac": achieved_ops / DP_PEAK_GOPS, "traffic": traffic,
