@@ -45,13 +45,14 @@ SMS = 152
 SM_MAX_MHZ = 2070.0
 DP_PEAK_GOPS = 2 * SMS * SM_MAX_MHZ / 1000.0
 
-# DRAM bytes per launch measured by ncu for the current kernel source (keyed by the SHA-256 of
-# the files that define it); a changed kernel reports null until it is profiled again.
+# DRAM bytes per launch measured by ncu, keyed by the SHA-256 of the files that define the
+# kernel and by the launch shape; a changed kernel or another shape reports null until it is
+# profiled again.
 NCU_TRAFFIC = {
     # one-pass ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the timed launch
     # itself: rhs_saturated_kernel<32,8>, z-chunk 16, 256^3 (717.35 + 632.97 MB); summary in
     # profiles/bench_256_launch_list.md.
-    "9967afc167d72b7e": 1350320000,
+    "9967afc167d72b7e:32x8, z-chunk 16": 1350320000,
 }
 
 
@@ -119,6 +120,13 @@ class ClockSampler:
         reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.strip().lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+def tile_text(tile) -> str:
+    """'32x8, z-chunk 16' or '16x16, balanced' for an (bx, by, kchunk[, flags]) tuple."""
+    from paper_2306_13002_gb300 import binding
+    bx, by, kc, flags = (tuple(tile) + (0, 0, 0, 0))[:4]
+    return f"{bx}x{by}, " + ("balanced" if flags & binding.TILE_BALANCED else f"z-chunk {kc}")
 
 
 def cpu_baseline(U: np.ndarray, budget_s: float = 10.0) -> dict:
@@ -362,7 +370,7 @@ def main() -> None:
     ap.add_argument("--ranker", action="store_true",
                     help="instead of the step benchmark: the rewriter-variant ranker study (512 variants at 256^3)")
     ap.add_argument("--variants", type=int, default=512)
-    ap.add_argument("--tile", default="", help="bx,by,kchunk: use this launch shape instead of the autotuner")
+    ap.add_argument("--tile", default="", help="bx,by,kchunk[,flags]: use this launch shape instead of the autotuner")
     ap.add_argument("--large", action="store_true",
                     help="instead of the step benchmark: RHS 512^3 and star stencil 768^3, all forms")
     args = ap.parse_args()
@@ -572,7 +580,7 @@ def main() -> None:
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     algo_bytes = in_bytes + out_bytes
     achieved_ops = DP_OPS_PER_POINT["rhs_saturated"] * points / (launch_ms * 1e-3) / 1e9
-    traffic = NCU_TRAFFIC.get(kernel_source_hash())
+    traffic = NCU_TRAFFIC.get(f"{kernel_source_hash()}:{tile_text(tuned_tile)}")
     result = {
         "metric": METRIC,
         "value": value,
@@ -587,7 +595,7 @@ def main() -> None:
         "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": f"rhs_saturated_{n}^3_fp64", "grid": [n] * 3, "halo": 2, "gamma": 1.4, "eps": 0.25,
-                   "tile": f"{tuned_tile[0]}x{tuned_tile[1]}, z-chunk {tuned_tile[2]}" + ("" if args.tile else " (acs_autotune_rhs)"), "l2": f"inputs larger than L2 ({in_bytes / 1e6:.0f} MB in, {out_bytes / 1e6:.0f} MB out)",
+                   "tile": tile_text(tuned_tile) + ("" if args.tile else " (acs_autotune_rhs)"), "l2": f"inputs larger than L2 ({in_bytes / 1e6:.0f} MB in, {out_bytes / 1e6:.0f} MB out)",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "alu", "achieved": achieved_ops, "peak": DP_PEAK_GOPS, "unit": "G FP64-pipe op/s",
                      "frac": achieved_ops / DP_PEAK_GOPS, "traffic": traffic,

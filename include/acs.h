@@ -106,13 +106,22 @@ typedef enum acs_form {
     ACS_FORM_SATURATED = 5
 } acs_form;
 
-/* Launch shape of a saturated kernel. A NULL tile selects the built-in default. */
+/* Launch shape of a saturated kernel. A NULL tile selects the built-in default (or the shape
+ * the autotuner recorded for the grid size). */
 typedef struct acs_tile {
     int bx;       /* threads (points) along x per block: 16, 32 or 64 */
     int by;       /* threads (points) along y per block: 4, 8 or 16 */
     int kchunk;   /* z-planes marched by one block; 0 = pick from the grid size */
-    int flags;    /* reserved, must be 0 */
+    int flags;    /* 0 or ACS_TILE_BALANCED (single-grid saturated calls only) */
 } acs_tile;
+
+/* acs_tile.flags: instead of one block per (column tile, z-chunk), launch one block per
+ * resident slot of the device and give every block an equal contiguous share of the
+ * (column tile, z-plane) work, so that no wave is partly filled; kchunk is then ignored.
+ * Accepted by acs_rhs_saturated, acs_rhs_saturated_host, acs_stencil_saturated and the
+ * single-grid autotuners; the batch entry points reject it (their blocks already take work
+ * from a queue). */
+#define ACS_TILE_BALANCED 1
 
 /*
  * acs_rhs_plain - as-written RHS, loop body (1) evaluated statement by statement.
@@ -130,7 +139,8 @@ acs_status acs_rhs_plain(const double *U, double *R, const acs_grid *g, const ac
  * the six neighbours, one reciprocal per point, dissipation reassociated as
  * sum(U at +-2) - 4 sum(U at +-1) + 18 U, FMA throughout, and every plane of U staged in
  * shared memory ahead of the arithmetic (bulk load). Same arguments as acs_rhs_plain plus
- *   tile   launch shape or NULL.
+ *   tile   launch shape or NULL (the autotuned shape for this grid size if acs_autotune_rhs
+ *          recorded one, else 16 x 16 with the balanced schedule).
  */
 acs_status acs_rhs_saturated(const double *U, double *R, const acs_grid *g, const acs_rhs_params *p,
                              const acs_tile *tile, acs_stream stream);
@@ -141,12 +151,15 @@ acs_status acs_rhs_saturated(const double *U, double *R, const acs_grid *g, cons
  *   U, R   host arrays in compact layout (in_sy = nx + 2 halo, in_sz = in_sy (ny + 2 halo),
  *          out_sy = nx, out_sz = nx ny; component strides free). Page-locked memory is
  *          needed for the copies to overlap; pageable memory works but serialises.
- *   ws     device workspace of acs_rhs_host_workspace_bytes(g, slab) bytes (two input and two
- *          output slab buffers), 16-byte aligned.
- * Uploads and downloads run on two library-owned streams per device; `stream` runs the kernels
- * and, on return, is ordered after the last download (so a later cudaStreamSynchronize(stream)
- * means R is complete on the host). Each input plane crosses the host link once (the halo
- * planes shared by consecutive slabs are copied on the device).
+ *   tile   launch shape of the slab kernels or NULL (16 x 16, balanced schedule).
+ *   ws     device workspace of acs_rhs_host_workspace_bytes(g, slab) bytes (three input and
+ *          three output slab buffers), 16-byte aligned.
+ * Uploads, the slab kernels (alternating between two streams) and downloads run on four
+ * library-owned streams per device, ordered by events; the first upload waits for the work
+ * already enqueued on `stream`, and on return `stream` is ordered after the last download (so a
+ * later cudaStreamSynchronize(stream) means R is complete on the host). Each input plane
+ * crosses the host link once (the halo planes shared by consecutive slabs are copied on the
+ * device by a small kernel).
  */
 size_t acs_rhs_host_workspace_bytes(const acs_grid *g, int slab);
 acs_status acs_rhs_saturated_host(const double *U, double *R, const acs_grid *g, const acs_rhs_params *p,
@@ -245,8 +258,8 @@ acs_status acs_batch_run_static(const acs_batch_item *items, int n, int kind, co
                                 const void *params, acs_stream stream);
 
 /* ---------------------------------------------------------------------------------------
- * Launch-shape autotuner. Each call times every built tile with several z-chunk lengths on
- * the caller's buffers (outputs are overwritten, `stream` is synchronised: do not capture),
+ * Launch-shape autotuner. Each call times every built tile with several z-chunk lengths (and,
+ * for the single-grid tuners, the balanced schedule, ACS_TILE_BALANCED) on the caller's buffers (outputs are overwritten, `stream` is synchronised: do not capture),
  * returns the fastest shape in `best` (and its time in `best_ms` if non-NULL) and records it
  * in a process-wide cache keyed by the workload shape. acs_rhs_saturated and
  * acs_stencil_saturated called with tile == NULL use the cached shape for their grid size.
@@ -257,7 +270,8 @@ acs_status acs_autotune_stencil(const double *u, const double *a, double *out, c
                                 const double *c, acs_tile *best, float *best_ms, acs_stream stream);
 acs_status acs_autotune_batch(const acs_batch_item *items, int n, int kind, const void *params, void *ws,
                               size_t ws_bytes, acs_tile *best, float *best_ms, acs_stream stream);
-/* Save / load (merge) / clear the tuning cache; a small versioned text file. */
+/* Save / load (merge) / clear the tuning cache; a small versioned text file ("acs-tune-cache 2"
+ * lines: bx by kchunk flags ms key; version-1 files, without the flags column, still load). */
 acs_status acs_tune_cache_save(const char *path);
 acs_status acs_tune_cache_load(const char *path);
 void acs_tune_cache_clear(void);

@@ -55,6 +55,7 @@ class BatchPlan(ctypes.Structure):
 
 
 KIND_RHS, KIND_STENCIL = 0, 1
+TILE_BALANCED = 1  # acs_tile.flags: one block per resident slot, equal (column, plane) shares
 VARIANT_NFEAT = 16
 
 
@@ -178,8 +179,8 @@ def _tile(tile) -> ctypes.POINTER(Tile) | None:
         return None
     if isinstance(tile, Tile):
         return ctypes.byref(tile)
-    bx, by, kchunk = (tuple(tile) + (0, 0, 0))[:3]
-    return ctypes.byref(Tile(int(bx), int(by), int(kchunk), 0))
+    bx, by, kchunk, flags = (tuple(tile) + (0, 0, 0, 0))[:4]
+    return ctypes.byref(Tile(int(bx), int(by), int(kchunk), int(flags)))
 
 
 def grid_for(inp, out, halo: int, ncomp: int) -> Grid:
@@ -337,7 +338,7 @@ def acs_autotune_rhs(U, R, gamma=1.4, eps=0.25, h=(1.0, 1.0, 1.0), halo=2, strea
     t, ms = Tile(), ctypes.c_float()
     _check(lib().acs_autotune_rhs(U.data_ptr(), R.data_ptr(), ctypes.byref(g), ctypes.byref(pr), ctypes.byref(t),
                                   ctypes.byref(ms), _stream_ptr(stream)), "acs_autotune_rhs")
-    return (t.bx, t.by, t.kchunk), ms.value
+    return (t.bx, t.by, t.kchunk, t.flags), ms.value
 
 
 def acs_autotune_stencil(u, a, out, c=None, halo=4, stream=None):
@@ -345,7 +346,7 @@ def acs_autotune_stencil(u, a, out, c=None, halo=4, stream=None):
     t, ms = Tile(), ctypes.c_float()
     _check(lib().acs_autotune_stencil(u.data_ptr(), a.data_ptr(), out.data_ptr(), ctypes.byref(g), _coef(c),
                                       ctypes.byref(t), ctypes.byref(ms), _stream_ptr(stream)), "acs_autotune_stencil")
-    return (t.bx, t.by, t.kchunk), ms.value
+    return (t.bx, t.by, t.kchunk, t.flags), ms.value
 
 
 def acs_autotune_batch(kind: int, grids, ws, params=None, halo=None, stream=None):
@@ -356,7 +357,7 @@ def acs_autotune_batch(kind: int, grids, ws, params=None, halo=None, stream=None
     _check(lib().acs_autotune_batch(items, len(grids), kind, ptr, ws.data_ptr(), nbytes, ctypes.byref(t),
                                     ctypes.byref(ms), _stream_ptr(stream)), "acs_autotune_batch")
     del keep
-    return (t.bx, t.by, t.kchunk), ms.value
+    return (t.bx, t.by, t.kchunk, t.flags), ms.value
 
 
 def acs_tune_cache_save(path: str) -> None:

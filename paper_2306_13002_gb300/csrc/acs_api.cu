@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <set>
 #include <utility>
@@ -48,6 +49,28 @@ acs_status ensure_smem(const void* fn, size_t bytes) {
         return launch_status("cudaFuncSetAttribute");
     g_attr_done.insert({fn, dev});
     return ACS_OK;
+}
+
+static std::mutex g_occ_mu;
+static std::map<std::pair<const void*, int>, int> g_occ;
+
+int resident_blocks(const void* fn, int threads, size_t smem_bytes) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    {
+        std::lock_guard<std::mutex> lk(g_occ_mu);
+        auto it = g_occ.find({fn, dev});
+        if (it != g_occ.end()) return it->second;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const int n = per_sm * num_sms();
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    g_occ[{fn, dev}] = n;
+    return n;
 }
 
 int num_sms() {
@@ -231,14 +254,14 @@ acs_status batch_params(int kind, const void* params, RhsConst& rk, StarCoef& sc
     return star_coef(static_cast<const double*>(params), sc);
 }
 
-const acs_tile kDefaultRhsTile = {32, 8, 0, 0};
+const acs_tile kDefaultRhsTile = {16, 16, 0, ACS_TILE_BALANCED};
 const acs_tile kDefaultStarTile = {32, 8, 0, 0};
 
 acs_status check_tile(const acs_tile* t, const acs_tile& def, bool (*supported)(int, int), acs_tile& out,
                       int kind = -1, const Geom* g = nullptr) {
     out = t ? *t : def;
     if (!t && g && tuned_tile(kind, *g, &out)) return ACS_OK;
-    if (out.flags != 0) return fail(ACS_ERR_INVALID, "tile flags must be 0");
+    if (out.flags & ~ACS_TILE_BALANCED) return fail(ACS_ERR_INVALID, "unknown tile flags 0x%x", out.flags);
     if (out.kchunk < 0) return fail(ACS_ERR_INVALID, "kchunk must be >= 0");
     if (!supported(out.bx, out.by)) return fail(ACS_ERR_UNSUPPORTED, "tile %dx%d is not built", out.bx, out.by);
     return ACS_OK;

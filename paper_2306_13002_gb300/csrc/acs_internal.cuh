@@ -95,5 +95,8 @@ size_t rhs_smem_bytes(int bx, int by);
 size_t star_smem_bytes(int bx, int by);
 int default_kchunk(int nz, i64 columns, int ctas_per_sm);
 int num_sms();
+// Blocks of `fn` that fit on the whole device at once (0 if the query fails); cached per
+// kernel and device. ensure_smem must have been called for fn first.
+int resident_blocks(const void* fn, int threads, size_t smem_bytes);
 
 }  // namespace acs

@@ -16,6 +16,7 @@ struct RhsShape {
     static constexpr size_t BYTES = sizeof(double) * (size_t)(U_ELEMS + FX_ELEMS + FY_ELEMS);
     static constexpr int NT = BX * BY;
     static constexpr int MINB = NT <= 256 ? 2 : 1;
+    static_assert(NT >= 2 * (BX + BY) && (2 * BX) % 32 == 0, "flux ring needs 2(BX+BY) threads, y-ring whole warps");
 };
 
 // The 12 non-trivial flux values of one point (component 0 of F_d is m_d itself).
@@ -106,27 +107,24 @@ __device__ __forceinline__ void rhs_march(const double* __restrict__ U, double* 
             Fxs[(c * BY + ty) * (BX + 2) + tx + 1] = pfx[c];
             Fys[(c * (BY + 2) + ty + 1) * BX + tx] = pfy[c];
         }
-        if (tid < 2 * (BX + BY)) {
-            int rx, ry;
-            const bool isx = tid < 2 * BY;
-            if (isx) {
-                ry = tid >> 1;
-                rx = (tid & 1) ? BX : -1;
-            } else {
-                const int t = tid - 2 * BY;
-                rx = t >> 1;
-                ry = (t & 1) ? BY : -1;
-            }
+        // The y-ring (rows -1 and BY) takes threads [0, 2 BX) and the x-ring (columns -1 and
+        // BX) the next 2 BY; 2 BX is a multiple of 32, so each warp computes one kind and
+        // only the four flux values it stores (the rest of point_flux is dead code there).
+        if (tid < 2 * BX) {
+            const int rx = tid >> 1, ry = (tid & 1) ? BY : -1;
             const int e = (ry + 2) * PX + (rx + 2);
             double fx[4], fy[4], fz[4];
             point_flux(s0[e], s0[PLANE + e], s0[2 * PLANE + e], s0[3 * PLANE + e], s0[4 * PLANE + e], k, fx, fy, fz);
-            if (isx) {
 #pragma unroll
-                for (int c = 0; c < 4; ++c) Fxs[(c * BY + ry) * (BX + 2) + rx + 1] = fx[c];
-            } else {
+            for (int c = 0; c < 4; ++c) Fys[(c * (BY + 2) + ry + 1) * BX + rx] = fy[c];
+        } else if (tid < 2 * (BX + BY)) {
+            const int t = tid - 2 * BX;
+            const int ry = t >> 1, rx = (t & 1) ? BX : -1;
+            const int e = (ry + 2) * PX + (rx + 2);
+            double fx[4], fy[4], fz[4];
+            point_flux(s0[e], s0[PLANE + e], s0[2 * PLANE + e], s0[3 * PLANE + e], s0[4 * PLANE + e], k, fx, fy, fz);
 #pragma unroll
-                for (int c = 0; c < 4; ++c) Fys[(c * (BY + 2) + ry + 1) * BX + rx] = fy[c];
-            }
+            for (int c = 0; c < 4; ++c) Fxs[(c * BY + ry) * (BX + 2) + rx + 1] = fx[c];
         }
         // (2) all fluxes of the own point at plane kk+1.
         {
@@ -227,6 +225,14 @@ __device__ __forceinline__ void star_march(const double* __restrict__ u, const d
     cp_async_wait_all();
     __syncthreads();
 
+    // The own column's values at planes kk-4 .. kk+4 live in registers (zq[m] = plane
+    // kk-4+m): the z-terms and the centre read no shared memory, and each step reads one new
+    // value (plane kk+5, the plane that has just landed). Only the x/y neighbours come from
+    // the ring. (Cells of inactive threads are read but never used.)
+    double zq[9];
+#pragma unroll
+    for (int m = 0; m < 9; ++m) zq[m] = slot(k0 - 4 + m)[own];
+
     const double* ap = a + (i64)(k0 + g.halo) * g.isz + (i64)(j + g.halo) * g.isy + (i + g.halo);
     for (int kk = k0; kk < k1; ++kk) {
         // Bulk-load the plane the next step needs into the slot of plane kk-5.
@@ -236,18 +242,21 @@ __device__ __forceinline__ void star_march(const double* __restrict__ u, const d
             const double av = __ldg(ap);
             const double* s0 = slot(kk);
             const Pipe& q = cf.pp;
-            double t = pmul(cf.c0, s0[own], q);
+            double t = pmul(cf.c0, zq[4], q);
 #pragma unroll
             for (int o = 1; o <= 4; ++o) t = fma(cf.c[o - 1], padd(s0[own + o], s0[own - o], q), t);
 #pragma unroll
             for (int o = 1; o <= 4; ++o) t = fma(cf.c[4 + o - 1], padd(s0[own + o * PX], s0[own - o * PX], q), t);
 #pragma unroll
-            for (int o = 1; o <= 4; ++o) t = fma(cf.c[8 + o - 1], padd(slot(kk + o)[own], slot(kk - o)[own], q), t);
+            for (int o = 1; o <= 4; ++o) t = fma(cf.c[8 + o - 1], padd(zq[4 + o], zq[4 - o], q), t);
             out[(i64)kk * g.osz + (i64)j * g.osy + i] = pmul(av, t, q);
         }
         ap += g.isz;
         cp_async_wait_all();
         __syncthreads();
+#pragma unroll
+        for (int m = 0; m < 8; ++m) zq[m] = zq[m + 1];
+        zq[8] = slot(kk + 5)[own];  // stale (and unused) once kk + 5 > k1 + 3
     }
 }
 

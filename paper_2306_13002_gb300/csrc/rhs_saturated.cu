@@ -38,10 +38,48 @@ __global__ void __launch_bounds__(BX * BY, RhsShape<BX, BY>::MINB)
     rhs_march<BX, BY>(U, R, g, k, blockIdx.x * BX, blockIdx.y * BY, k0, min(k0 + kchunk, g.nz), smem);
 }
 
+// Balanced schedule (ACS_TILE_BALANCED): one block per resident slot. The work is the list
+// of (column tile, z-plane) pairs, columns in x-fastest order and each column's planes in
+// order; block b marches the contiguous share [W b / G, W (b + 1) / G) of its W pairs, which
+// is one or two column segments. Every block gets the same number of planes (to one), so
+// there is no partly filled last wave, and a grid of C columns pays about C + G segment
+// warm-ups instead of one per z-chunk.
+template <int BX, int BY>
+__global__ void __launch_bounds__(BX * BY, RhsShape<BX, BY>::MINB)
+    rhs_saturated_balanced_kernel(const double* __restrict__ U, double* __restrict__ R, Geom g, RhsConst k) {
+    extern __shared__ __align__(16) double smem[];
+    const int ntx = (g.nx + BX - 1) / BX;
+    const i64 W = (i64)ntx * ((g.ny + BY - 1) / BY) * g.nz;
+    i64 L = W * blockIdx.x / gridDim.x;
+    const i64 L1 = W * (blockIdx.x + 1) / gridDim.x;
+    while (L < L1) {
+        const i64 col = L / g.nz;
+        const int z0 = (int)(L - col * g.nz);
+        const int z1 = (int)min((i64)g.nz, z0 + (L1 - L));
+        rhs_march<BX, BY>(U, R, g, k, (int)(col % ntx) * BX, (int)(col / ntx) * BY, z0, z1, smem);
+        L += z1 - z0;
+    }
+}
 
 template <int BX, int BY>
-acs_status launch_t(const double* U, double* R, const Geom& g, const RhsConst& k, int kchunk, cudaStream_t s) {
+acs_status launch_balanced(const double* U, double* R, const Geom& g, const RhsConst& k, cudaStream_t s) {
     using S = RhsShape<BX, BY>;
+    const void* fn = (const void*)rhs_saturated_balanced_kernel<BX, BY>;
+    acs_status st = ensure_smem(fn, S::BYTES);
+    if (st != ACS_OK) return st;
+    const i64 W = (i64)((g.nx + BX - 1) / BX) * ((g.ny + BY - 1) / BY) * g.nz;
+    i64 G = resident_blocks(fn, S::NT, S::BYTES);
+    if (G <= 0) return fail(ACS_ERR_CUDA, "occupancy query failed for rhs_saturated_balanced_kernel");
+    if (G > W) G = W;
+    rhs_saturated_balanced_kernel<BX, BY><<<(unsigned)G, dim3(BX, BY, 1), S::BYTES, s>>>(U, R, g, k);
+    return launch_status("rhs_saturated_balanced_kernel");
+}
+
+template <int BX, int BY>
+acs_status launch_t(const double* U, double* R, const Geom& g, const RhsConst& k, int kchunk, int flags,
+                    cudaStream_t s) {
+    using S = RhsShape<BX, BY>;
+    if (flags & ACS_TILE_BALANCED) return launch_balanced<BX, BY>(U, R, g, k, s);
     const void* fn = (const void*)rhs_saturated_kernel<BX, BY>;
     acs_status st = ensure_smem(fn, S::BYTES);
     if (st != ACS_OK) return st;
@@ -74,12 +112,12 @@ size_t rhs_smem_bytes(int bx, int by) {
 
 acs_status launch_rhs_saturated(const double* U, double* R, const Geom& g, const RhsConst& k, const acs_tile& t,
                                 cudaStream_t s) {
-    if (t.bx == 32 && t.by == 8) return launch_t<32, 8>(U, R, g, k, t.kchunk, s);
-    if (t.bx == 32 && t.by == 4) return launch_t<32, 4>(U, R, g, k, t.kchunk, s);
-    if (t.bx == 32 && t.by == 16) return launch_t<32, 16>(U, R, g, k, t.kchunk, s);
-    if (t.bx == 16 && t.by == 8) return launch_t<16, 8>(U, R, g, k, t.kchunk, s);
-    if (t.bx == 16 && t.by == 16) return launch_t<16, 16>(U, R, g, k, t.kchunk, s);
-    if (t.bx == 64 && t.by == 4) return launch_t<64, 4>(U, R, g, k, t.kchunk, s);
+    if (t.bx == 32 && t.by == 8) return launch_t<32, 8>(U, R, g, k, t.kchunk, t.flags, s);
+    if (t.bx == 32 && t.by == 4) return launch_t<32, 4>(U, R, g, k, t.kchunk, t.flags, s);
+    if (t.bx == 32 && t.by == 16) return launch_t<32, 16>(U, R, g, k, t.kchunk, t.flags, s);
+    if (t.bx == 16 && t.by == 8) return launch_t<16, 8>(U, R, g, k, t.kchunk, t.flags, s);
+    if (t.bx == 16 && t.by == 16) return launch_t<16, 16>(U, R, g, k, t.kchunk, t.flags, s);
+    if (t.bx == 64 && t.by == 4) return launch_t<64, 4>(U, R, g, k, t.kchunk, t.flags, s);
     return fail(ACS_ERR_UNSUPPORTED, "rhs tile %dx%d is not built", t.bx, t.by);
 }
 

@@ -50,10 +50,42 @@ __global__ void __launch_bounds__(BX * BY) star_saturated_kernel(const double* _
     star_march<BX, BY>(u, a, out, g, cf, blockIdx.x * BX, blockIdx.y * BY, k0, min(k0 + kchunk, g.nz), smem);
 }
 
+// Balanced schedule (ACS_TILE_BALANCED): one block per resident slot, each marching an equal
+// contiguous share of the (column tile, z-plane) list, as rhs_saturated_balanced_kernel does.
+template <int BX, int BY>
+__global__ void __launch_bounds__(BX * BY) star_saturated_balanced_kernel(const double* __restrict__ u,
+                                                                          const double* __restrict__ a,
+                                                                          double* __restrict__ out, Geom g,
+                                                                          StarCoef cf) {
+    extern __shared__ __align__(16) double smem[];
+    const int ntx = (g.nx + BX - 1) / BX;
+    const i64 W = (i64)ntx * ((g.ny + BY - 1) / BY) * g.nz;
+    i64 L = W * blockIdx.x / gridDim.x;
+    const i64 L1 = W * (blockIdx.x + 1) / gridDim.x;
+    while (L < L1) {
+        const i64 col = L / g.nz;
+        const int z0 = (int)(L - col * g.nz);
+        const int z1 = (int)min((i64)g.nz, z0 + (L1 - L));
+        star_march<BX, BY>(u, a, out, g, cf, (int)(col % ntx) * BX, (int)(col / ntx) * BY, z0, z1, smem);
+        L += z1 - z0;
+    }
+}
+
 template <int BX, int BY>
 acs_status launch_star_t(const double* u, const double* a, double* out, const Geom& g, const StarCoef& c, int kchunk,
-                         cudaStream_t s) {
+                         int flags, cudaStream_t s) {
     using S = StarShape<BX, BY>;
+    if (flags & ACS_TILE_BALANCED) {
+        const void* fb = (const void*)star_saturated_balanced_kernel<BX, BY>;
+        acs_status st = ensure_smem(fb, S::BYTES);
+        if (st != ACS_OK) return st;
+        const i64 W = (i64)((g.nx + BX - 1) / BX) * ((g.ny + BY - 1) / BY) * g.nz;
+        i64 G = resident_blocks(fb, S::NT, S::BYTES);
+        if (G <= 0) return fail(ACS_ERR_CUDA, "occupancy query failed for star_saturated_balanced_kernel");
+        if (G > W) G = W;
+        star_saturated_balanced_kernel<BX, BY><<<(unsigned)G, dim3(BX, BY, 1), S::BYTES, s>>>(u, a, out, g, c);
+        return launch_status("star_saturated_balanced_kernel");
+    }
     const void* fn = (const void*)star_saturated_kernel<BX, BY>;
     acs_status st = ensure_smem(fn, S::BYTES);
     if (st != ACS_OK) return st;
@@ -98,12 +130,12 @@ acs_status launch_stencil_plain(const double* u, const double* a, double* out, c
 
 acs_status launch_stencil_saturated(const double* u, const double* a, double* out, const Geom& g, const StarCoef& c,
                                     const acs_tile& t, cudaStream_t s) {
-    if (t.bx == 32 && t.by == 8) return launch_star_t<32, 8>(u, a, out, g, c, t.kchunk, s);
-    if (t.bx == 32 && t.by == 4) return launch_star_t<32, 4>(u, a, out, g, c, t.kchunk, s);
-    if (t.bx == 32 && t.by == 16) return launch_star_t<32, 16>(u, a, out, g, c, t.kchunk, s);
-    if (t.bx == 64 && t.by == 4) return launch_star_t<64, 4>(u, a, out, g, c, t.kchunk, s);
-    if (t.bx == 64 && t.by == 8) return launch_star_t<64, 8>(u, a, out, g, c, t.kchunk, s);
-    if (t.bx == 16 && t.by == 16) return launch_star_t<16, 16>(u, a, out, g, c, t.kchunk, s);
+    if (t.bx == 32 && t.by == 8) return launch_star_t<32, 8>(u, a, out, g, c, t.kchunk, t.flags, s);
+    if (t.bx == 32 && t.by == 4) return launch_star_t<32, 4>(u, a, out, g, c, t.kchunk, t.flags, s);
+    if (t.bx == 32 && t.by == 16) return launch_star_t<32, 16>(u, a, out, g, c, t.kchunk, t.flags, s);
+    if (t.bx == 64 && t.by == 4) return launch_star_t<64, 4>(u, a, out, g, c, t.kchunk, t.flags, s);
+    if (t.bx == 64 && t.by == 8) return launch_star_t<64, 8>(u, a, out, g, c, t.kchunk, t.flags, s);
+    if (t.bx == 16 && t.by == 16) return launch_star_t<16, 16>(u, a, out, g, c, t.kchunk, t.flags, s);
     return fail(ACS_ERR_UNSUPPORTED, "stencil tile %dx%d is not built", t.bx, t.by);
 }
 

@@ -2,7 +2,8 @@
 //
 // The paper leaves the parallel structure to the directive compiler and notes that the
 // shape of the parallelism decides performance (Sec. II-C). Here the shape is ours to
-// choose: the tuner times every built tile (BX x BY) with a few z-chunk lengths on the
+// choose: the tuner times every built tile (BX x BY) with a few z-chunk lengths and with the
+// balanced one-block-per-slot schedule (single grids) on the
 // caller's own buffers (CUDA events on the caller's stream, best of three launches after a
 // warm-up), and records the fastest per workload shape in a process-wide cache. A saturated
 // call with tile == NULL uses the cached shape for its grid size when there is one.
@@ -38,7 +39,9 @@ std::string key_of(int kind, const Geom* g, int n) {
 
 const int kRhsTiles[][2] = {{32, 8}, {32, 4}, {32, 16}, {16, 8}, {16, 16}, {64, 4}};
 const int kStarTiles[][2] = {{32, 8}, {32, 4}, {32, 16}, {64, 4}, {64, 8}, {16, 16}};
-const int kChunks[] = {8, 16, 32, 64};
+// z-chunk candidates; kBalanced stands for the balanced schedule (ACS_TILE_BALANCED).
+constexpr int kBalanced = -1;
+const int kChunks[] = {8, 16, 32, 64, kBalanced};
 
 struct Timer {
     cudaEvent_t a = nullptr, b = nullptr;
@@ -77,8 +80,9 @@ acs_status tune_grid(int kind, const Geom& g, const int (*tiles)[2], int ntiles,
     float bms = 1e30f;
     for (int q = 0; q < ntiles; ++q) {
         for (int kc : kChunks) {
-            if (kc > g.nz && kc != kChunks[0]) continue;
+            if (kc > g.nz && kc != kChunks[0] && kc != kBalanced) continue;
             acs_tile cand = {tiles[q][0], tiles[q][1], kc, 0};
+            if (kc == kBalanced) cand = acs_tile{tiles[q][0], tiles[q][1], 0, ACS_TILE_BALANCED};
             float ms = 0.f;
             acs_status st = time_best([&]() { return launch(cand); }, s, t, ms);
             if (st != ACS_OK) return st;
@@ -158,10 +162,10 @@ acs_status tune_cache_save(const char* path) {
     FILE* f = fopen(path, "w");
     if (!f) return fail(ACS_ERR_INVALID, "cannot open %s for writing", path);
     std::lock_guard<std::mutex> lk(g_mu);
-    fprintf(f, "acs-tune-cache 1\n");
+    fprintf(f, "acs-tune-cache 2\n");
     for (auto& kv : g_cache)
-        fprintf(f, "%d %d %d %.6f %s\n", kv.second.tile.bx, kv.second.tile.by, kv.second.tile.kchunk, kv.second.ms,
-                kv.first.c_str());
+        fprintf(f, "%d %d %d %d %.6f %s\n", kv.second.tile.bx, kv.second.tile.by, kv.second.tile.kchunk,
+                kv.second.tile.flags, kv.second.ms, kv.first.c_str());
     fclose(f);
     return ACS_OK;
 }
@@ -170,26 +174,40 @@ acs_status tune_cache_load(const char* path) {
     FILE* f = fopen(path, "r");
     if (!f) return fail(ACS_ERR_INVALID, "cannot open %s", path);
     char line[4096];
-    if (!fgets(line, sizeof(line), f) || strncmp(line, "acs-tune-cache 1", 16) != 0) {
+    // Version 1 lines: bx by kchunk ms key. Version 2 adds the tile flags after kchunk.
+    int version = 0;
+    if (fgets(line, sizeof(line), f)) {
+        if (strncmp(line, "acs-tune-cache 1", 16) == 0) version = 1;
+        if (strncmp(line, "acs-tune-cache 2", 16) == 0) version = 2;
+    }
+    if (version == 0) {
         fclose(f);
-        return fail(ACS_ERR_INVALID, "%s is not an autotune cache (version 1)", path);
+        return fail(ACS_ERR_INVALID, "%s is not an autotune cache (version 1 or 2)", path);
     }
     std::map<std::string, Entry> loaded;
     while (fgets(line, sizeof(line), f)) {
-        int bx, by, kc;
+        int bx, by, kc, flags = 0;
         float ms;
         char key[4000];
-        if (sscanf(line, "%d %d %d %f %3999s", &bx, &by, &kc, &ms, key) != 5) {
+        const int got = version == 1 ? sscanf(line, "%d %d %d %f %3999s", &bx, &by, &kc, &ms, key)
+                                     : sscanf(line, "%d %d %d %d %f %3999s", &bx, &by, &kc, &flags, &ms, key);
+        if (got != (version == 1 ? 5 : 6)) {
             fclose(f);
             return fail(ACS_ERR_INVALID, "malformed autotune cache line: %s", line);
         }
         const bool rhs_key = key[0] == '0' || key[0] == '2';
+        const bool batch_key = key[0] == '2' || key[0] == '3';
         const bool ok = rhs_key ? rhs_tile_supported(bx, by) : star_tile_supported(bx, by);
-        if (!ok || kc < 1) {
+        if (!ok) {
             fclose(f);
             return fail(ACS_ERR_INVALID, "autotune cache names an unbuilt tile %dx%d", bx, by);
         }
-        loaded[key] = Entry{acs_tile{bx, by, kc, 0}, ms};
+        const bool balanced = flags == ACS_TILE_BALANCED && !batch_key;
+        if ((flags != 0 && !balanced) || (!balanced && kc < 1) || (balanced && kc != 0)) {
+            fclose(f);
+            return fail(ACS_ERR_INVALID, "autotune cache line with bad z-chunk %d / flags %d", kc, flags);
+        }
+        loaded[key] = Entry{acs_tile{bx, by, kc, flags}, ms};
     }
     fclose(f);
     std::lock_guard<std::mutex> lk(g_mu);

@@ -93,7 +93,8 @@ def test_rhs_rejects_short_strides(lib):
 
 def test_saturated_rejects_unbuilt_tile_and_flags(lib):
     assert _call_rhs(lib, FAKE_U, FAKE_R, _grid(), _params(), sat=True, tile=(24, 8, 0, 0)) == 4
-    assert _call_rhs(lib, FAKE_U, FAKE_R, _grid(), _params(), sat=True, tile=(32, 8, 0, 1)) == 1
+    assert _call_rhs(lib, FAKE_U, FAKE_R, _grid(), _params(), sat=True, tile=(32, 8, 0, 2)) == 1
+    assert _call_rhs(lib, FAKE_U, FAKE_R, _grid(), _params(), sat=True, tile=(32, 8, 0, 3)) == 1
     assert _call_rhs(lib, FAKE_U, FAKE_R, _grid(), _params(), sat=True, tile=(32, 8, -1, 0)) == 1
 
 
@@ -129,6 +130,8 @@ def test_batch_prepare_rejects_bad_arguments(lib):
     assert lib.acs_batch_prepare(bad, 1, 1, None, WS, need, ctypes.byref(plan), None) == 7     # alias
     t = binding.Tile(24, 8, 8, 0)
     assert lib.acs_batch_prepare(items, 2, 1, ctypes.byref(t), WS, need, ctypes.byref(plan), None) == 4
+    t = binding.Tile(32, 8, 8, binding.TILE_BALANCED)   # the batch takes work from its own queue
+    assert lib.acs_batch_prepare(items, 2, 1, ctypes.byref(t), WS, need, ctypes.byref(plan), None) == 1
 
 
 def test_batch_launch_rejects_unprepared_plan(lib):

@@ -53,7 +53,8 @@ def test_rhs_32cubed_full(form):
 
 
 @pytest.mark.parametrize("dims", [(1, 1, 1), (3, 5, 2), (37, 29, 23), (33, 9, 17), (64, 8, 5), (70, 21, 40)])
-@pytest.mark.parametrize("tile", [None, (16, 8, 3), (32, 4, 1), (64, 4, 7), (32, 16, 0), (16, 16, 2)])
+@pytest.mark.parametrize("tile", [None, (16, 8, 3), (32, 4, 1), (64, 4, 7), (32, 16, 0), (16, 16, 2),
+                                  (32, 8, 0, 1), (16, 16, 0, 1), (64, 4, 0, 1)])
 def test_rhs_saturated_ragged(dims, tile):
     nx, ny, nz = dims
     U = inputs.rhs_field(nx, ny, nz, halo=2, seed=1000 + nx * 7 + ny * 3 + nz)
@@ -159,7 +160,8 @@ def test_stencil_48cubed_full(form):
 
 
 @pytest.mark.parametrize("dims", [(1, 1, 1), (5, 3, 2), (37, 29, 23), (65, 9, 17), (100, 33, 12)])
-@pytest.mark.parametrize("tile", [None, (32, 4, 3), (64, 8, 0), (16, 16, 5), (64, 4, 1), (32, 16, 2)])
+@pytest.mark.parametrize("tile", [None, (32, 4, 3), (64, 8, 0), (16, 16, 5), (64, 4, 1), (32, 16, 2),
+                                  (32, 8, 0, 1), (16, 16, 0, 1), (64, 4, 0, 1)])
 def test_stencil_saturated_ragged(dims, tile):
     nx, ny, nz = dims
     u, a = inputs.stencil_fields(nx, ny, nz, seed=4000 + nx + 5 * ny + 11 * nz)
