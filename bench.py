@@ -49,10 +49,11 @@ DP_PEAK_GOPS = 2 * SMS * SM_MAX_MHZ / 1000.0
 # kernel and by the launch shape; a changed kernel or another shape reports null until it is
 # profiled again.
 NCU_TRAFFIC = {
-    # one-pass ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the timed launch
-    # itself: rhs_saturated_kernel<32,8>, z-chunk 16, 256^3 (717.35 + 632.97 MB); summary in
+    # one-pass ncu captures (dram__bytes_read.sum + dram__bytes_write.sum) of one launch at
+    # 256^3, the 4th after 3 warm-ups, in the shape the autotuner picks; summary in
     # profiles/bench_256_launch_list.md.
-    "9967afc167d72b7e:32x8, z-chunk 16": 1350320000,
+    "e20eabb54c8c0d29:16x16, balanced": 1410000000 + 643050000,
+    "e20eabb54c8c0d29:32x8, balanced": 1560000000 + 644090000,
 }
 
 

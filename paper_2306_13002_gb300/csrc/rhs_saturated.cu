@@ -40,10 +40,14 @@ __global__ void __launch_bounds__(BX * BY, RhsShape<BX, BY>::MINB)
 
 // Balanced schedule (ACS_TILE_BALANCED): one block per resident slot. The work is the list
 // of (column tile, z-plane) pairs, columns in x-fastest order and each column's planes in
-// order; block b marches the contiguous share [W b / G, W (b + 1) / G) of its W pairs, which
-// is one or two column segments. Every block gets the same number of planes (to one), so
-// there is no partly filled last wave, and a grid of C columns pays about C + G segment
-// warm-ups instead of one per z-chunk.
+// order; block b marches the contiguous share [W b / G, W (b + 1) / G) of its W pairs (one
+// or two column segments when G exceeds the column count, whole columns plus two partial
+// ones otherwise). Every block gets the same number of planes (to one), so there is no partly
+// filled last wave, and a grid of C columns pays about C + G segment warm-ups instead of one
+// per z-chunk. Neighbouring columns run at different z, so their shared halo planes are read
+// from DRAM again (about 2x the input bytes); a variant that kept all blocks at the same z
+// (whole-column rounds, then base/top shares) read 1.18x the input but ran 0.3-1.4 % slower
+// on GB300, and this kernel is bound by the FP64 pipe, not by DRAM.
 template <int BX, int BY>
 __global__ void __launch_bounds__(BX * BY, RhsShape<BX, BY>::MINB)
     rhs_saturated_balanced_kernel(const double* __restrict__ U, double* __restrict__ R, Geom g, RhsConst k) {

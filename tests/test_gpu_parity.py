@@ -63,6 +63,17 @@ def test_rhs_saturated_ragged(dims, tile):
     assert_parity(R, ref, what=f"rhs saturated {dims} tile {tile}")
 
 
+@pytest.mark.parametrize("dims,tile", [((288, 288, 5), (16, 16, 0, 1)), ((288, 290, 4), (32, 8, 0, 1))])
+def test_rhs_balanced_whole_rounds(dims, tile):
+    """More column tiles than resident blocks (324 > 2 x 152): balanced shares that span
+    several whole columns."""
+    nx, ny, nz = dims
+    U = inputs.rhs_field(nx, ny, nz, halo=2, seed=1500 + ny)
+    ref = oracle.rhs(U, threads=4)
+    R = _rhs_gpu("saturated", U, tile=tile).cpu().numpy()
+    assert_parity(R, ref, what=f"rhs balanced {dims} tile {tile}")
+
+
 @pytest.mark.parametrize("dims", [(1, 1, 1), (37, 29, 23), (70, 21, 40)])
 def test_rhs_plain_ragged(dims):
     nx, ny, nz = dims
@@ -151,6 +162,15 @@ def test_rhs_256cubed_sampled_planes(form):
 
 
 # --------------------------------------------------------------------------- stencil
+
+@pytest.mark.parametrize("dims,tile", [((320, 500, 3), (32, 8, 0, 1)), ((400, 400, 2), (16, 16, 0, 1))])
+def test_stencil_balanced_whole_rounds(dims, tile):
+    """More column tiles than resident blocks (620 and 625 > 4 x 152) under the balanced schedule."""
+    nx, ny, nz = dims
+    u, a = inputs.stencil_fields(nx, ny, nz, seed=4500 + nx)
+    ref = oracle.stencil(u, a, threads=4)
+    assert_parity(_star_gpu("saturated", u, a, tile=tile).cpu().numpy(), ref, what=f"stencil balanced {dims} {tile}")
+
 
 @pytest.mark.parametrize("form", ["plain", "saturated"])
 def test_stencil_48cubed_full(form):
