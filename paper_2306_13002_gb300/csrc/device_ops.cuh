@@ -15,13 +15,17 @@ struct Geom {
     i64 osy, osz, osc;
 };
 
-// FP64 instruction selection for the saturated kernels. On GB300 the FP64 pipe issues DFMA
-// at ~1.96 operations/clock/SM but DADD and DMUL at only ~1.65 (measured). Every add,
-// subtract and multiply of the saturated forms is therefore issued as an FMA whose extra
-// operand is a runtime 1.0, -1.0 or -0.0 held in a kernel argument, which the compiler
-// cannot fold back into a DADD/DMUL. The results are bit-identical to the plain
-// operations: the product by +-1 is exact and the FMA rounds once, and adding -0.0 to a
-// product leaves every value (including the sign of zero) unchanged.
+// FP64 instruction selection for the saturated kernels. Measured on GB300: an FP64
+// instruction whose operands are two per-thread registers and nothing else from a register
+// (DADD, DMUL, or a DFMA whose third operand is an immediate or a kernel argument) issues at
+// 1.60 operations/clock/SM, while a DFMA with three register operands (or with one) issues
+// at 1.88-1.90. Every add, subtract and multiply of the saturated forms is therefore an FMA
+// with a 1.0, -1.0 or -0.0 operand, and every constant operand (these three and the folded
+// coefficients) is staged through shared memory into an ordinary register at the start of a
+// block's work (stage_consts), so the compiler can neither fold it back nor address it in the
+// constant bank. The results are bit-identical to the plain operations: the product by +-1 is
+// exact and the FMA rounds once, and adding -0.0 to a product leaves every value (including
+// the sign of zero) unchanged.
 struct Pipe {
     double one, mone, nz;   // 1.0, -1.0, -0.0
 };
@@ -58,15 +62,29 @@ struct StarCoef {
 // far below one ulp, so the result is within about one ulp of the correctly rounded 1/x.
 // Outside [2^-1000, 2^1000] (zero, subnormal, huge, inf, NaN) it falls back to an IEEE
 // division; the test of the exponent is integer work only.
-__device__ __forceinline__ double rcp_refined(double x) {
+// `one` is 1.0 (in a register, see Pipe).
+__device__ __forceinline__ double rcp_refined(double x, double one) {
     const int hi = __double2hiint(x);
     const int bexp = (hi >> 20) & 0x7ff;
     if (bexp < 23 || bexp > 2023) return 1.0 / x;
     double y;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-    double e = fma(-x, y, 1.0);
+    double e = fma(-x, y, one);
     e = fma(e, e, e);
     return fma(y, e, y);
+}
+
+// Copies a struct of doubles (kernel-argument constants) through shared memory into
+// registers: thread 0 writes it to `buf` before a barrier (stage_consts_write), every thread
+// reads it back after that barrier (stage_consts_read).
+template <class T>
+__device__ __forceinline__ void stage_consts_write(double* buf, const T& v, int tid) {
+    static_assert(sizeof(T) % sizeof(double) == 0, "a struct of doubles");
+    if (tid == 0) *reinterpret_cast<T*>(buf) = v;
+}
+template <class T>
+__device__ __forceinline__ T stage_consts_read(const double* buf) {
+    return *reinterpret_cast<const T*>(buf);
 }
 
 // cp.async helpers (8-byte element copies global -> shared, L1-bypassing variant not

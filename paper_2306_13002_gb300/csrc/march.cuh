@@ -13,10 +13,18 @@ struct RhsShape {
     static constexpr int U_ELEMS = NSLOT * 5 * PLANE;
     static constexpr int FX_ELEMS = 4 * BY * (BX + 2);
     static constexpr int FY_ELEMS = 4 * (BY + 2) * BX;
-    static constexpr size_t BYTES = sizeof(double) * (size_t)(U_ELEMS + FX_ELEMS + FY_ELEMS);
+    static constexpr int CONST_ELEMS = 16;   // staged constants (RhsRegs)
+    static constexpr size_t BYTES = sizeof(double) * (size_t)(U_ELEMS + FX_ELEMS + FY_ELEMS + CONST_ELEMS);
     static constexpr int NT = BX * BY;
     static constexpr int MINB = NT <= 256 ? 2 : 1;
     static_assert(NT >= 2 * (BX + BY) && (2 * BX) % 32 == 0, "flux ring needs 2(BX+BY) threads, y-ring whole warps");
+};
+
+// The constants of the RHS march as register values: the folded coefficients and Pipe, and
+// the two dissipation weights.
+struct RhsRegs {
+    RhsConst k;
+    double m4, c18;   // -4, 18
 };
 
 // The 12 non-trivial flux values of one point (component 0 of F_d is m_d itself).
@@ -25,7 +33,7 @@ struct RhsShape {
 __device__ __forceinline__ void point_flux(double rho, double mx, double my, double mz, double E, const RhsConst& k,
                                            double fx[4], double fy[4], double fz[4]) {
     const Pipe& q = k.pp;
-    const double r = rcp_refined(rho);
+    const double r = rcp_refined(rho, q.one);
     const double vx = pmul(mx, r, q), vy = pmul(my, r, q), vz = pmul(mz, r, q);
     const double mxvx = pmul(mx, vx, q);
     const double twoKE = fma(mz, vz, fma(my, vy, mxvx));
@@ -71,12 +79,14 @@ __device__ __forceinline__ void load_plane(double* slot, const double* __restric
 // threads past a barrier after their last shared-memory read, so the caller may reuse smem.
 template <int BX, int BY>
 __device__ __forceinline__ void rhs_march(const double* __restrict__ U, double* __restrict__ R, const Geom& g,
-                                          const RhsConst& k, int i0, int j0, int k0, int k1, double* smem) {
+                                          const RhsConst& kc, int i0, int j0, int k0, int k1, double* smem) {
     using S = RhsShape<BX, BY>;
     constexpr int PX = S::PX, PLANE = S::PLANE;
     double* Us = smem;
     double* Fxs = smem + S::U_ELEMS;
     double* Fys = Fxs + S::FX_ELEMS;
+    double* Cs = Fys + S::FY_ELEMS;
+    static_assert(sizeof(RhsRegs) <= S::CONST_ELEMS * sizeof(double), "constant staging area");
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
     const int i = i0 + tx, j = j0 + ty;
@@ -84,11 +94,14 @@ __device__ __forceinline__ void rhs_march(const double* __restrict__ U, double* 
     const int own = (ty + 2) * PX + (tx + 2);
     auto slot = [&](int q) -> double* { return Us + ((q + S::NSLOT) % S::NSLOT) * (5 * PLANE); };
 
-    // Prologue: planes k0-2 .. k0+2.
+    // Prologue: planes k0-2 .. k0+2, and the constants into registers.
+    stage_consts_write(Cs, RhsRegs{kc, -4.0, 18.0}, tid);
     for (int q = k0 - 2; q <= k0 + 2; ++q) load_plane<BX, BY>(slot(q), U, g, i0, j0, q, tid);
     cp_async_commit();
     cp_async_wait_all();
     __syncthreads();
+    const RhsRegs kr = stage_consts_read<RhsRegs>(Cs);
+    const RhsConst& k = kr.k;
 
     double fzm[4], fz0[4], fzp[4], pfx[4], pfy[4];
     {
@@ -164,8 +177,8 @@ __device__ __forceinline__ void rhs_march(const double* __restrict__ U, double* 
                                        padd(sm2[cb], sp2[cb], q), q);
                 const double s1 = padd(padd(padd(s0[cb - 1], s0[cb + 1], q), padd(s0[cb - PX], s0[cb + PX], q), q),
                                        padd(sm1[cb], sp1[cb], q), q);
-                double dd = fma(-4.0, s1, s2);
-                dd = fma(18.0, s0[cb], dd);
+                double dd = fma(kr.m4, s1, s2);
+                dd = fma(kr.c18, s0[cb], dd);
                 Rp[(i64)c * g.osc] = fma(k.neps, dd, fl);
             }
         }
