@@ -200,8 +200,12 @@ template <int BX, int BY>
 struct StarShape {
     static constexpr int PX = BX + 8, PY = BY + 8, PLANE = PX * PY;
     static constexpr int NSLOT = 10;
-    static constexpr size_t BYTES = sizeof(double) * (size_t)NSLOT * PLANE;
+    static constexpr int CONST_ELEMS = 16;   // staged StarCoef
+    static constexpr size_t BYTES = sizeof(double) * ((size_t)NSLOT * PLANE + CONST_ELEMS);
     static constexpr int NT = BX * BY;
+    // Blocks per SM the launch bounds ask registers for: 2048 threads per SM at most (and the
+    // shared memory allows it for every built tile).
+    static constexpr int MINB = NT >= 512 ? 2 : 4;
 };
 
 template <int BX, int BY>
@@ -223,7 +227,7 @@ __device__ __forceinline__ void load_star_plane(double* slot, const double* __re
 // threads past a barrier after their last shared-memory read.
 template <int BX, int BY>
 __device__ __forceinline__ void star_march(const double* __restrict__ u, const double* __restrict__ a,
-                                           double* __restrict__ out, const Geom& g, const StarCoef& cf, int i0, int j0,
+                                           double* __restrict__ out, const Geom& g, const StarCoef& cfc, int i0, int j0,
                                            int k0, int k1, double* smem) {
     using S = StarShape<BX, BY>;
     constexpr int PX = S::PX, PLANE = S::PLANE;
@@ -233,10 +237,14 @@ __device__ __forceinline__ void star_march(const double* __restrict__ u, const d
     const int own = (ty + 4) * PX + (tx + 4);
     auto slot = [&](int q) -> double* { return smem + ((q + S::NSLOT) % S::NSLOT) * PLANE; };
 
+    double* Cs = smem + S::NSLOT * PLANE;
+    static_assert(sizeof(StarCoef) <= S::CONST_ELEMS * sizeof(double), "constant staging area");
+    stage_consts_write(Cs, cfc, tid);
     for (int q = k0 - 4; q <= k0 + 4; ++q) load_star_plane<BX, BY>(slot(q), u, g, i0, j0, q, tid);
     cp_async_commit();
     cp_async_wait_all();
     __syncthreads();
+    const StarCoef cf = stage_consts_read<StarCoef>(Cs);   // the weights in registers (see Pipe)
 
     // The own column's values at planes kk-4 .. kk+4 live in registers (zq[m] = plane
     // kk-4+m): the z-terms and the centre read no shared memory, and each step reads one new

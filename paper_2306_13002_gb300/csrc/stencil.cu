@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(256) star_plain_kernel(const double* u, const 
 }
 
 template <int BX, int BY>
-__global__ void __launch_bounds__(BX * BY) star_saturated_kernel(const double* __restrict__ u,
+__global__ void __launch_bounds__(BX * BY, StarShape<BX, BY>::MINB) star_saturated_kernel(const double* __restrict__ u,
                                                                  const double* __restrict__ a,
                                                                  double* __restrict__ out, Geom g, StarCoef cf,
                                                                  int kchunk) {
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(BX * BY) star_saturated_kernel(const double* _
 // Balanced schedule (ACS_TILE_BALANCED): one block per resident slot, each marching an equal
 // contiguous share of the (column tile, z-plane) list, as rhs_saturated_balanced_kernel does.
 template <int BX, int BY>
-__global__ void __launch_bounds__(BX * BY) star_saturated_balanced_kernel(const double* __restrict__ u,
+__global__ void __launch_bounds__(BX * BY, StarShape<BX, BY>::MINB) star_saturated_balanced_kernel(const double* __restrict__ u,
                                                                           const double* __restrict__ a,
                                                                           double* __restrict__ out, Geom g,
                                                                           StarCoef cf) {
