@@ -111,26 +111,35 @@ __global__ void __launch_bounds__(256) block_cse_kernel(const double* A, const d
     }
 }
 
-// Saturated form: one thread per point; the three loop-invariant products are folded once
-// (t1, t2, 2 t1, -q4 t2, t1 q3), G(p) and its diagonal terms are computed once, every add,
-// subtract and multiply is issued as an FMA (Pipe), and the pointers are __restrict__, so the
+// Saturated form: one thread per point; the loop-invariant products are folded once
+// (t2, -t1, -t2, 2 t1, -q4 t2, t1 q3) and held in registers like the Pipe constants, G(p)
+// and its diagonal terms are computed once, every add, subtract and multiply is issued as an
+// FMA (Pipe), and the pointers are __restrict__, so the
 // compiler may hoist loads of later entries over earlier stores as far as registers allow
 // (bulk load bounded by the register file instead of all 151 loads at once).
 __global__ void __launch_bounds__(256) block_saturated_kernel(const double* __restrict__ A,
                                                               const double* __restrict__ B,
                                                               const double* __restrict__ G,
                                                               double* __restrict__ out, Geom g, BlkArgs a) {
+    // The folded constants and Pipe staged through shared memory into registers (see Pipe).
+    __shared__ double cs[11];
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const double t1 = a.dt * a.q1, t2 = a.dt * a.q2;
+        const double v[11] = {1.0, -1.0, -0.0, t2, -t1, -t2, 2.0 * t1, -a.q4 * t2, t1 * a.q3, 2.0, 1.0};
+        for (int q = 0; q < 11; ++q) cs[q] = v[q];
+    }
+    __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= g.nx || j >= g.ny) return;
-    const Pipe pp = Pipe{1.0, -1.0, -0.0};
-    const double t1 = a.dt * a.q1, t2 = a.dt * a.q2;
-    const double nt1 = -t1, nt2 = -t2, tw1 = 2.0 * t1, nq4t2 = -a.q4 * t2, t1q3 = t1 * a.q3;
+    const Pipe pp = Pipe{cs[0], cs[1], cs[2]};
+    const double t2 = cs[3], nt1 = cs[4], nt2 = cs[5], tw1 = cs[6], nq4t2 = cs[7], t1q3 = cs[8], two = cs[9],
+                 one = cs[10];
     for (int k = blockIdx.z; k < g.nz; k += gridDim.z) {
         const i64 p = (i64)(k + g.halo) * g.isz + (i64)(j + g.halo) * g.isy + (i64)(i + g.halo);
         const i64 o = (i64)k * g.osz + (i64)j * g.osy + i;
         const double tg = pmul(t1q3, __ldg(G + p), pp);
-        const double dg = fma(2.0, tg, 1.0);
+        const double dg = fma(two, tg, one);
 #pragma unroll
         for (int q = 0; q < 25; ++q) {
             const double* Aq = A + (i64)q * g.isc + p;
