@@ -50,10 +50,10 @@ DP_PEAK_GOPS = 2 * SMS * SM_MAX_MHZ / 1000.0
 # profiled again.
 NCU_TRAFFIC = {
     # one-pass ncu captures (dram__bytes_read.sum + dram__bytes_write.sum) of one launch at
-    # 256^3, the 4th after 3 warm-ups, in the shape the autotuner picks; summary in
+    # 256^3, the 4th after 3 warm-ups, in the shapes the autotuner picks; summary in
     # profiles/bench_256_launch_list.md.
-    "e20eabb54c8c0d29:16x16, balanced": 1410000000 + 643050000,
-    "e20eabb54c8c0d29:32x8, balanced": 1560000000 + 644090000,
+    "fbef47f9269a540c:16x16, balanced": 1410000000 + 643050000,
+    "fbef47f9269a540c:32x8, balanced": 1560000000 + 644120000,
 }
 
 
