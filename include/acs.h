@@ -112,7 +112,7 @@ typedef struct acs_tile {
     int bx;       /* threads (points) along x per block: 16, 32 or 64 */
     int by;       /* threads (points) along y per block: 4, 8 or 16 */
     int kchunk;   /* z-planes marched by one block; 0 = pick from the grid size */
-    int flags;    /* 0 or ACS_TILE_BALANCED (single-grid saturated calls only) */
+    int flags;    /* 0, ACS_TILE_BALANCED and / or ACS_TILE_TMA (single-grid saturated calls) */
 } acs_tile;
 
 /* acs_tile.flags: instead of one block per (column tile, z-chunk), launch one block per
@@ -122,6 +122,14 @@ typedef struct acs_tile {
  * single-grid autotuners; the batch entry points reject it (their blocks already take work
  * from a queue). */
 #define ACS_TILE_BALANCED 1
+/* acs_tile.flags: stage each xy-plane of the input into shared memory with one tensor copy
+ * (TMA, cp.async.bulk.tensor) completing on an mbarrier, instead of element-wise cp.async.
+ * Built for acs_stencil_saturated (and its autotuner); ACS_ERR_UNSUPPORTED from the other
+ * entry points. Used where the layout allows it (16-byte aligned input, row and plane strides
+ * that are multiples of 2 elements, even halo); other layouts are staged element-wise, with
+ * the same results. Waits on the mbarriers are bounded (about one second); one that runs out
+ * is counted (acs_wait_timeouts) and the call's results are then wrong, but the kernel ends. */
+#define ACS_TILE_TMA 2
 
 /*
  * acs_rhs_plain - as-written RHS, loop body (1) evaluated statement by statement.
@@ -187,6 +195,9 @@ acs_status acs_stencil_plain(const double *u, const double *a, double *out, cons
  *   out = a(p) * (C0 u(p) + sum_d sum_o c[d][o] (u(p+o e_d) + u(p-o e_d))),
  *   C0 = -2 sum c (folded on the host), FMA throughout, u planes staged in shared memory
  *   and reused by the 9 z-offsets as the block marches along z.
+ *   tile   launch shape or NULL (the autotuned shape for this grid size if
+ *          acs_autotune_stencil recorded one, else 32 x 8, z-chunks from the grid size, TMA
+ *          plane staging where the layout allows it).
  */
 acs_status acs_stencil_saturated(const double *u, const double *a, double *out, const acs_grid *g,
                                  const double *c, const acs_tile *tile, acs_stream stream);
@@ -354,6 +365,14 @@ acs_status acs_block_form(const double *A, const double *B, const double *G, dou
 
 /* Static text for a status code. */
 const char *acs_status_string(acs_status s);
+
+/*
+ * acs_wait_timeouts - how many bounded device-side waits (TMA plane staging) have run out on
+ * the current device since the library was loaded; 0 in normal operation. Synchronous: reads a
+ * device counter with cudaMemcpy, so call it after the work has completed (for instance after
+ * cudaStreamSynchronize). ACS_ERR_INVALID for a NULL count, ACS_ERR_CUDA if the read fails.
+ */
+acs_status acs_wait_timeouts(unsigned int *count);
 
 /* Reason for the calling thread's most recent failed call ("" if none). */
 const char *acs_last_error(void);

@@ -56,6 +56,7 @@ class BatchPlan(ctypes.Structure):
 
 KIND_RHS, KIND_STENCIL = 0, 1
 TILE_BALANCED = 1  # acs_tile.flags: one block per resident slot, equal (column, plane) shares
+TILE_TMA = 2       # acs_tile.flags: planes staged by TMA tensor copies (star stencil)
 VARIANT_NFEAT = 16
 
 
@@ -81,7 +82,7 @@ EXPORTS = ("acs_rhs_plain", "acs_rhs_saturated", "acs_rhs_form", "acs_stencil_pl
            "acs_variant_build", "acs_variant_launch", "acs_variant_free", "acs_ranker_param_count",
            "acs_ranker_workspace_bytes", "acs_ranker_train", "acs_variant_rank", "acs_status_string",
            "acs_last_error", "acs_abi_version", "acs_block_form", "acs_rhs_host_workspace_bytes",
-           "acs_rhs_saturated_host")
+           "acs_rhs_saturated_host", "acs_wait_timeouts")
 
 
 def lib() -> ctypes.CDLL:
@@ -153,6 +154,8 @@ def lib() -> ctypes.CDLL:
             L.acs_status_string.restype = ctypes.c_char_p
             L.acs_last_error.restype = ctypes.c_char_p
             L.acs_abi_version.restype = ctypes.c_int
+            L.acs_wait_timeouts.argtypes = [ctypes.POINTER(ctypes.c_uint)]
+            L.acs_wait_timeouts.restype = st
             _lib = L
     return _lib
 
@@ -258,6 +261,14 @@ def acs_stencil_saturated(u, a, out, c=None, halo: int = 4, tile=None, stream=No
         raise ValueError("u and a must have the same shape and strides")
     _check(lib().acs_stencil_saturated(u.data_ptr(), a.data_ptr(), out.data_ptr(), ctypes.byref(g), _coef(c),
                                        _tile(tile), _stream_ptr(stream)), "acs_stencil_saturated")
+
+
+def acs_wait_timeouts() -> int:
+    """Bounded device-side waits that ran out on the current device (0 in normal operation);
+    synchronous, call it after the work has completed."""
+    n = ctypes.c_uint(0)
+    _check(lib().acs_wait_timeouts(ctypes.byref(n)), "acs_wait_timeouts")
+    return int(n.value)
 
 
 def acs_status_string(status: int) -> str:

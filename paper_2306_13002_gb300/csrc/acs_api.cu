@@ -73,6 +73,62 @@ int resident_blocks(const void* fn, int threads, size_t smem_bytes) {
     return n;
 }
 
+static __device__ unsigned int g_wait_timeouts = 0;
+
+unsigned* wait_timeout_counter() {
+    static std::mutex mu;
+    static unsigned* addr[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_wait_timeouts) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        addr[dev] = static_cast<unsigned*>(p);
+    }
+    return addr[dev];
+}
+
+acs_status encode_plane_map(const double* base, const Geom& g, int ncomp, int box_x, int box_y, CUtensorMap* map) {
+    if ((uintptr_t)base % 16 != 0) return fail(ACS_ERR_ALIGN, "TMA staging needs a 16-byte aligned input");
+    if (g.isy % 2 != 0 || g.isz % 2 != 0 || (ncomp > 1 && g.isc % 2 != 0))
+        return fail(ACS_ERR_ALIGN, "TMA staging needs row, plane and component strides of whole 16-byte units");
+    if (g.halo % 2 != 0) return fail(ACS_ERR_ALIGN, "TMA staging needs an even halo (box x origin 16-byte aligned)");
+    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static std::mutex mu;
+    static Encode encode = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!encode) {
+            void* fn = nullptr;
+            cudaDriverEntryPointQueryResult q;
+            if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                    cudaSuccess ||
+                q != cudaDriverEntryPointSuccess || !fn) {
+                cudaGetLastError();
+                return fail(ACS_ERR_UNSUPPORTED, "the driver has no cuTensorMapEncodeTiled");
+            }
+            encode = reinterpret_cast<Encode>(fn);
+        }
+    }
+    const int rank = ncomp > 1 ? 4 : 3;
+    const cuuint64_t dims[4] = {(cuuint64_t)g.nx + 2 * g.halo, (cuuint64_t)g.ny + 2 * g.halo,
+                                (cuuint64_t)g.nz + 2 * g.halo, (cuuint64_t)ncomp};
+    const cuuint64_t strides[3] = {(cuuint64_t)g.isy * 8, (cuuint64_t)g.isz * 8, (cuuint64_t)g.isc * 8};
+    const cuuint32_t box[4] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1, (cuuint32_t)ncomp};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, rank, const_cast<double*>(base), dims, strides,
+                              box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(ACS_ERR_ALIGN, "cuTensorMapEncodeTiled rejected the input layout (error %d)", (int)r);
+    return ACS_OK;
+}
+
 int num_sms() {
     static int cached[64] = {0};
     int dev = 0;
@@ -255,13 +311,15 @@ acs_status batch_params(int kind, const void* params, RhsConst& rk, StarCoef& sc
 }
 
 const acs_tile kDefaultRhsTile = {16, 16, 0, ACS_TILE_BALANCED};
-const acs_tile kDefaultStarTile = {32, 8, 0, 0};
+const acs_tile kDefaultStarTile = {32, 8, 0, ACS_TILE_TMA};
 
 acs_status check_tile(const acs_tile* t, const acs_tile& def, bool (*supported)(int, int), acs_tile& out,
                       int kind = -1, const Geom* g = nullptr) {
     out = t ? *t : def;
     if (!t && g && tuned_tile(kind, *g, &out)) return ACS_OK;
-    if (out.flags & ~ACS_TILE_BALANCED) return fail(ACS_ERR_INVALID, "unknown tile flags 0x%x", out.flags);
+    if (out.flags & ~(ACS_TILE_BALANCED | ACS_TILE_TMA)) return fail(ACS_ERR_INVALID, "unknown tile flags 0x%x", out.flags);
+    if ((out.flags & ACS_TILE_TMA) && kind != ACS_KIND_STENCIL)
+        return fail(ACS_ERR_UNSUPPORTED, "TMA plane staging is built for the star stencil");
     if (out.kchunk < 0) return fail(ACS_ERR_INVALID, "kchunk must be >= 0");
     if (!supported(out.bx, out.by)) return fail(ACS_ERR_UNSUPPORTED, "tile %dx%d is not built", out.bx, out.by);
     return ACS_OK;
@@ -575,6 +633,14 @@ const char* acs_status_string(acs_status s) {
 }
 
 const char* acs_last_error(void) { return t_err; }
+
+acs_status acs_wait_timeouts(unsigned int* count) {
+    if (!count) return fail(ACS_ERR_INVALID, "count is NULL");
+    unsigned* p = wait_timeout_counter();
+    if (!p) return fail(ACS_ERR_CUDA, "cannot address the wait-timeout counter");
+    if (cudaMemcpy(count, p, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return launch_status("cudaMemcpy");
+    return ACS_OK;
+}
 
 int acs_abi_version(void) { return 100; }
 

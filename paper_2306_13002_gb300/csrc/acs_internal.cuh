@@ -1,6 +1,7 @@
 // Internal host-side declarations shared by the C-ABI layer and the kernel launchers.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -95,6 +96,15 @@ size_t rhs_smem_bytes(int bx, int by);
 size_t star_smem_bytes(int bx, int by);
 int default_kchunk(int nz, i64 columns, int ctas_per_sm);
 int num_sms();
+// Device address of the counter of bounded waits that ran out (see tma.cuh), for the
+// current device; NULL if it cannot be obtained.
+unsigned* wait_timeout_counter();
+// 3D (ncomp == 1) or 4D (ncomp == 5, component stride in_sc) tensor map of a halo-extended
+// input for TMA plane staging, box bx x by x 1 (x 1 x ncomp). ACS_ERR_ALIGN when the base is
+// not 16-byte aligned, a stride is not a multiple of 16 bytes or the halo is odd (the box's x
+// origin i0 - r + halo must be a multiple of 2 elements).
+acs_status encode_plane_map(const double* base, const Geom& g, int ncomp, int box_x, int box_y, CUtensorMap* map);
+
 // Blocks of `fn` that fit on the whole device at once (0 if the query fails); cached per
 // kernel and device. ensure_smem must have been called for fn first.
 int resident_blocks(const void* fn, int threads, size_t smem_bytes);

@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(BX * BY, KIND == ACS_KIND_RHS ? RhsShape<BX, B
         if (KIND == ACS_KIND_RHS)
             rhs_march<BX, BY>(d.in0, d.out, d.g, rk, tx * BX, ty * BY, k0, k1, smem);
         else
-            star_march<BX, BY>(d.in0, d.in1, d.out, d.g, sc, tx * BX, ty * BY, k0, k1, smem);
+            star_march<BX, BY, false>(d.in0, d.in1, d.out, d.g, sc, tx * BX, ty * BY, k0, k1, smem, nullptr, nullptr);
     }
 }
 

@@ -3,6 +3,7 @@
 #pragma once
 
 #include "acs_internal.cuh"
+#include "tma.cuh"
 
 namespace acs {
 
@@ -201,11 +202,14 @@ struct StarShape {
     static constexpr int PX = BX + 8, PY = BY + 8, PLANE = PX * PY;
     static constexpr int NSLOT = 10;
     static constexpr int CONST_ELEMS = 16;   // staged StarCoef
-    static constexpr size_t BYTES = sizeof(double) * ((size_t)NSLOT * PLANE + CONST_ELEMS);
+    // Ring, staged constants, one mbarrier per slot (TMA staging), and 128 bytes to align the
+    // ring for TMA.
+    static constexpr size_t BYTES = sizeof(double) * ((size_t)NSLOT * PLANE + CONST_ELEMS + NSLOT) + 128;
     static constexpr int NT = BX * BY;
     // Blocks per SM the launch bounds ask registers for: 2048 threads per SM at most (and the
     // shared memory allows it for every built tile).
     static constexpr int MINB = NT >= 512 ? 2 : 4;
+    static_assert((PLANE * sizeof(double)) % 128 == 0, "every ring slot 128-byte aligned");
 };
 
 template <int BX, int BY>
@@ -225,24 +229,57 @@ __device__ __forceinline__ void load_star_plane(double* slot, const double* __re
 
 // One block's work: the BX x BY column tile at (i0, j0), z-planes [k0, k1). Ends with all
 // threads past a barrier after their last shared-memory read.
-template <int BX, int BY>
+//
+// Plane staging: with TMA = false every thread copies its share of a plane element by element
+// (cp.async); with TMA = true thread 0 copies the whole (BX+8) x (BY+8) box of plane q with one
+// tensor copy (`map`: the 3D tensor map of u) that completes on the slot's mbarrier, and the
+// readers wait on that mbarrier (bounded; timeouts counted in *tmo). The box of plane q is
+// the q-th plane's fill number n = (q - k0 + 4) / 10 of its slot, so its phase parity is n & 1.
+template <int BX, int BY, bool TMA>
 __device__ __forceinline__ void star_march(const double* __restrict__ u, const double* __restrict__ a,
                                            double* __restrict__ out, const Geom& g, const StarCoef& cfc, int i0, int j0,
-                                           int k0, int k1, double* smem) {
+                                           int k0, int k1, double* smem_raw, const CUtensorMap* map, unsigned* tmo) {
     using S = StarShape<BX, BY>;
     constexpr int PX = S::PX, PLANE = S::PLANE;
+    constexpr unsigned kPlaneBytes = PLANE * sizeof(double);
+    double* smem = align128(smem_raw);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
     const int i = i0 + tx, j = j0 + ty;
     const bool active = (i < g.nx) && (j < g.ny);
     const int own = (ty + 4) * PX + (tx + 4);
-    auto slot = [&](int q) -> double* { return smem + ((q + S::NSLOT) % S::NSLOT) * PLANE; };
+    auto sidx = [&](int q) -> int { return (q + S::NSLOT) % S::NSLOT; };
+    auto slot = [&](int q) -> double* { return smem + sidx(q) * PLANE; };
 
     double* Cs = smem + S::NSLOT * PLANE;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(Cs + S::CONST_ELEMS);
     static_assert(sizeof(StarCoef) <= S::CONST_ELEMS * sizeof(double), "constant staging area");
+    auto parity = [&](int q) -> unsigned { return (unsigned)((q - k0 + 4) / S::NSLOT) & 1u; };
+    auto issue = [&](int q) {   // thread 0 only
+        uint64_t* bar = bars + sidx(q);
+        mbar_arrive_expect_tx(bar, kPlaneBytes);
+        tma_load_3d(slot(q), map, bar, i0 - 4 + g.halo, j0 - 4 + g.halo, q + g.halo);
+    };
+    bool ok = true;                          // this thread's waits have all completed
+    int lost = 0x7fffffff;                   // thread 0: the plane whose wait ran out
+
     stage_consts_write(Cs, cfc, tid);
-    for (int q = k0 - 4; q <= k0 + 4; ++q) load_star_plane<BX, BY>(slot(q), u, g, i0, j0, q, tid);
-    cp_async_commit();
-    cp_async_wait_all();
+    if (TMA) {
+        if (tid == 0) {
+            for (int s = 0; s < S::NSLOT; ++s) mbar_init(bars + s, 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+        if (tid == 0)
+            for (int q = k0 - 4; q <= k0 + 4; ++q) issue(q);
+        for (int q = k0 - 4; q <= k0 + 4 && ok; ++q) {
+            ok = mbar_wait_bounded(bars + sidx(q), parity(q), tmo);
+            if (!ok) lost = q;
+        }
+    } else {
+        for (int q = k0 - 4; q <= k0 + 4; ++q) load_star_plane<BX, BY>(slot(q), u, g, i0, j0, q, tid);
+        cp_async_commit();
+        cp_async_wait_all();
+    }
     __syncthreads();
     const StarCoef cf = stage_consts_read<StarCoef>(Cs);   // the weights in registers (see Pipe)
 
@@ -256,9 +293,18 @@ __device__ __forceinline__ void star_march(const double* __restrict__ u, const d
 
     const double* ap = a + (i64)(k0 + g.halo) * g.isz + (i64)(j + g.halo) * g.isy + (i + g.halo);
     for (int kk = k0; kk < k1; ++kk) {
-        // Bulk-load the plane the next step needs into the slot of plane kk-5.
-        if (kk + 5 <= k1 + 3) load_star_plane<BX, BY>(slot(kk + 5), u, g, i0, j0, kk + 5, tid);
-        cp_async_commit();
+        // Bulk-load the plane the next step needs into the slot of plane kk-5 (read last in
+        // step kk-5, several barriers ago).
+        const bool next = kk + 5 <= k1 + 3;
+        if (TMA) {
+            if (next && tid == 0 && ok) {
+                fence_proxy_async();
+                issue(kk + 5);
+            }
+        } else {
+            if (next) load_star_plane<BX, BY>(slot(kk + 5), u, g, i0, j0, kk + 5, tid);
+            cp_async_commit();
+        }
         if (active) {
             const double av = __ldg(ap);
             const double* s0 = slot(kk);
@@ -273,11 +319,26 @@ __device__ __forceinline__ void star_march(const double* __restrict__ u, const d
             out[(i64)kk * g.osz + (i64)j * g.osy + i] = pmul(av, t, q);
         }
         ap += g.isz;
-        cp_async_wait_all();
+        if (TMA) {
+            if (next && ok) {
+                ok = mbar_wait_bounded(bars + sidx(kk + 5), parity(kk + 5), tmo);
+                if (!ok) lost = kk + 5;
+            }
+        } else {
+            cp_async_wait_all();
+        }
         __syncthreads();
 #pragma unroll
         for (int m = 0; m < 8; ++m) zq[m] = zq[m + 1];
-        zq[8] = slot(kk + 5)[own];  // stale (and unused) once kk + 5 > k1 + 3
+        if (kk + 1 < k1) zq[8] = slot(kk + 5)[own];
+    }
+    if (TMA) {
+        // A copy whose wait ran out may still be in flight: give it one more bounded wait
+        // before the slots are reused or the block exits. Then retire the barriers.
+        if (tid == 0 && !ok) mbar_wait_bounded(bars + sidx(lost), parity(lost), tmo);
+        __syncthreads();
+        if (tid == 0)
+            for (int s = 0; s < S::NSLOT; ++s) mbar_inval(bars + s);
     }
 }
 

@@ -11,9 +11,13 @@
 // i.e. the common factor a(p) is pulled out of the twelve terms (distributivity expressed
 // through ASSOC/COMM and FMA1), the twelve copies of -2u(p) merge into one term, and each
 // pair of symmetric neighbours is summed before its single FMA. Adds and multiplies are
-// issued as FMAs with runtime +-1 / -0 operands (faster on GB300, bit-identical). The xy-planes of u with a
-// 4-cell halo live in a ten-slot shared-memory ring: the nine planes k-4..k+4 in use plus
-// the plane being prefetched with cp.async for the next step.
+// issued as FMAs with 1 / -0 operands, and the weights and those operands sit in registers
+// (faster on GB300, bit-identical; see Pipe). The xy-planes of u with a 4-cell halo live in a
+// ten-slot shared-memory ring: the nine planes k-4..k+4 in use plus the plane being
+// prefetched for the next step, element by element with cp.async or, with ACS_TILE_TMA, as
+// one tensor copy per plane (TMA) completing on the slot's mbarrier.
+#include <cstring>
+
 #include "march.cuh"
 
 namespace acs {
@@ -40,23 +44,23 @@ __global__ void __launch_bounds__(256) star_plain_kernel(const double* u, const 
     }
 }
 
-template <int BX, int BY>
-__global__ void __launch_bounds__(BX * BY, StarShape<BX, BY>::MINB) star_saturated_kernel(const double* __restrict__ u,
-                                                                 const double* __restrict__ a,
-                                                                 double* __restrict__ out, Geom g, StarCoef cf,
-                                                                 int kchunk) {
+template <int BX, int BY, bool TMA>
+__global__ void __launch_bounds__(BX * BY, StarShape<BX, BY>::MINB)
+    star_saturated_kernel(const double* __restrict__ u, const double* __restrict__ a, double* __restrict__ out,
+                          Geom g, StarCoef cf, int kchunk, const __grid_constant__ CUtensorMap map, unsigned* tmo) {
     extern __shared__ __align__(16) double smem[];
     const int k0 = blockIdx.z * kchunk;
-    star_march<BX, BY>(u, a, out, g, cf, blockIdx.x * BX, blockIdx.y * BY, k0, min(k0 + kchunk, g.nz), smem);
+    star_march<BX, BY, TMA>(u, a, out, g, cf, blockIdx.x * BX, blockIdx.y * BY, k0, min(k0 + kchunk, g.nz), smem,
+                            &map, tmo);
 }
 
 // Balanced schedule (ACS_TILE_BALANCED): one block per resident slot, each marching an equal
 // contiguous share of the (column tile, z-plane) list, as rhs_saturated_balanced_kernel does.
-template <int BX, int BY>
-__global__ void __launch_bounds__(BX * BY, StarShape<BX, BY>::MINB) star_saturated_balanced_kernel(const double* __restrict__ u,
-                                                                          const double* __restrict__ a,
-                                                                          double* __restrict__ out, Geom g,
-                                                                          StarCoef cf) {
+template <int BX, int BY, bool TMA>
+__global__ void __launch_bounds__(BX * BY, StarShape<BX, BY>::MINB)
+    star_saturated_balanced_kernel(const double* __restrict__ u, const double* __restrict__ a,
+                                   double* __restrict__ out, Geom g, StarCoef cf,
+                                   const __grid_constant__ CUtensorMap map, unsigned* tmo) {
     extern __shared__ __align__(16) double smem[];
     const int ntx = (g.nx + BX - 1) / BX;
     const i64 W = (i64)ntx * ((g.ny + BY - 1) / BY) * g.nz;
@@ -66,27 +70,31 @@ __global__ void __launch_bounds__(BX * BY, StarShape<BX, BY>::MINB) star_saturat
         const i64 col = L / g.nz;
         const int z0 = (int)(L - col * g.nz);
         const int z1 = (int)min((i64)g.nz, z0 + (L1 - L));
-        star_march<BX, BY>(u, a, out, g, cf, (int)(col % ntx) * BX, (int)(col / ntx) * BY, z0, z1, smem);
+        star_march<BX, BY, TMA>(u, a, out, g, cf, (int)(col % ntx) * BX, (int)(col / ntx) * BY, z0, z1, smem, &map,
+                                tmo);
         L += z1 - z0;
     }
 }
 
-template <int BX, int BY>
-acs_status launch_star_t(const double* u, const double* a, double* out, const Geom& g, const StarCoef& c, int kchunk,
-                         int flags, cudaStream_t s) {
+template <int BX, int BY, bool TMA>
+acs_status launch_star_tt(const double* u, const double* a, double* out, const Geom& g, const StarCoef& c, int kchunk,
+                          int flags, const CUtensorMap& map, cudaStream_t s) {
     using S = StarShape<BX, BY>;
+    unsigned* tmo = wait_timeout_counter();
+    if (!tmo) return fail(ACS_ERR_CUDA, "cannot address the wait-timeout counter");
     if (flags & ACS_TILE_BALANCED) {
-        const void* fb = (const void*)star_saturated_balanced_kernel<BX, BY>;
+        const void* fb = (const void*)star_saturated_balanced_kernel<BX, BY, TMA>;
         acs_status st = ensure_smem(fb, S::BYTES);
         if (st != ACS_OK) return st;
         const i64 W = (i64)((g.nx + BX - 1) / BX) * ((g.ny + BY - 1) / BY) * g.nz;
         i64 G = resident_blocks(fb, S::NT, S::BYTES);
         if (G <= 0) return fail(ACS_ERR_CUDA, "occupancy query failed for star_saturated_balanced_kernel");
         if (G > W) G = W;
-        star_saturated_balanced_kernel<BX, BY><<<(unsigned)G, dim3(BX, BY, 1), S::BYTES, s>>>(u, a, out, g, c);
+        star_saturated_balanced_kernel<BX, BY, TMA><<<(unsigned)G, dim3(BX, BY, 1), S::BYTES, s>>>(u, a, out, g, c,
+                                                                                                   map, tmo);
         return launch_status("star_saturated_balanced_kernel");
     }
-    const void* fn = (const void*)star_saturated_kernel<BX, BY>;
+    const void* fn = (const void*)star_saturated_kernel<BX, BY, TMA>;
     acs_status st = ensure_smem(fn, S::BYTES);
     if (st != ACS_OK) return st;
     if (kchunk <= 0) {
@@ -99,8 +107,20 @@ acs_status launch_star_t(const double* u, const double* a, double* out, const Ge
     }
     dim3 block(BX, BY, 1);
     dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, (g.nz + kchunk - 1) / kchunk);
-    star_saturated_kernel<BX, BY><<<grid, block, S::BYTES, s>>>(u, a, out, g, c, kchunk);
+    star_saturated_kernel<BX, BY, TMA><<<grid, block, S::BYTES, s>>>(u, a, out, g, c, kchunk, map, tmo);
     return launch_status("star_saturated_kernel");
+}
+
+template <int BX, int BY>
+acs_status launch_star_t(const double* u, const double* a, double* out, const Geom& g, const StarCoef& c, int kchunk,
+                         int flags, cudaStream_t s) {
+    CUtensorMap map;
+    memset(&map, 0, sizeof(map));
+    // TMA staging where the layout allows it (the box: the tile plus its 4-cell halo, one
+    // plane of the halo-extended u); element-wise staging otherwise, with the same results.
+    if ((flags & ACS_TILE_TMA) && encode_plane_map(u, g, 1, BX + 8, BY + 8, &map) == ACS_OK)
+        return launch_star_tt<BX, BY, true>(u, a, out, g, c, kchunk, flags, map, s);
+    return launch_star_tt<BX, BY, false>(u, a, out, g, c, kchunk, flags, map, s);
 }
 
 }  // namespace

@@ -3,7 +3,8 @@
 // The paper leaves the parallel structure to the directive compiler and notes that the
 // shape of the parallelism decides performance (Sec. II-C). Here the shape is ours to
 // choose: the tuner times every built tile (BX x BY) with a few z-chunk lengths and with the
-// balanced one-block-per-slot schedule (single grids) on the
+// balanced one-block-per-slot schedule (single grids), for the star stencil each both with
+// element-wise and with TMA plane staging, on the
 // caller's own buffers (CUDA events on the caller's stream, best of three launches after a
 // warm-up), and records the fastest per workload shape in a process-wide cache. A saturated
 // call with tile == NULL uses the cached shape for its grid size when there is one.
@@ -72,8 +73,8 @@ acs_status time_best(F run, cudaStream_t s, Timer& t, float& ms) {
 }
 
 template <class Launch>
-acs_status tune_grid(int kind, const Geom& g, const int (*tiles)[2], int ntiles, Launch launch, cudaStream_t s,
-                     acs_tile* best, float* best_ms) {
+acs_status tune_grid(int kind, const Geom& g, const int (*tiles)[2], int ntiles, const int* staging, int nstaging,
+                     Launch launch, cudaStream_t s, acs_tile* best, float* best_ms) {
     Timer t;
     if (!t.init()) return launch_status("cudaEventCreate");
     acs_tile bt = {0, 0, 0, 0};
@@ -81,14 +82,16 @@ acs_status tune_grid(int kind, const Geom& g, const int (*tiles)[2], int ntiles,
     for (int q = 0; q < ntiles; ++q) {
         for (int kc : kChunks) {
             if (kc > g.nz && kc != kChunks[0] && kc != kBalanced) continue;
-            acs_tile cand = {tiles[q][0], tiles[q][1], kc, 0};
-            if (kc == kBalanced) cand = acs_tile{tiles[q][0], tiles[q][1], 0, ACS_TILE_BALANCED};
-            float ms = 0.f;
-            acs_status st = time_best([&]() { return launch(cand); }, s, t, ms);
-            if (st != ACS_OK) return st;
-            if (ms < bms) {
-                bms = ms;
-                bt = cand;
+            for (int f = 0; f < nstaging; ++f) {
+                acs_tile cand = {tiles[q][0], tiles[q][1], kc, staging[f]};
+                if (kc == kBalanced) cand = acs_tile{tiles[q][0], tiles[q][1], 0, ACS_TILE_BALANCED | staging[f]};
+                float ms = 0.f;
+                acs_status st = time_best([&]() { return launch(cand); }, s, t, ms);
+                if (st != ACS_OK) return st;
+                if (ms < bms) {
+                    bms = ms;
+                    bt = cand;
+                }
             }
         }
     }
@@ -113,15 +116,17 @@ bool tuned_tile(int kind, const Geom& g, acs_tile* t) {
 
 acs_status tune_rhs(const double* U, double* R, const Geom& g, const RhsConst& k, cudaStream_t s, acs_tile* best,
                     float* best_ms) {
+    static const int staging[] = {0};
     return tune_grid(
-        ACS_KIND_RHS, g, kRhsTiles, 6, [&](const acs_tile& c) { return launch_rhs_saturated(U, R, g, k, c, s); }, s, best,
-        best_ms);
+        ACS_KIND_RHS, g, kRhsTiles, 6, staging, 1,
+        [&](const acs_tile& c) { return launch_rhs_saturated(U, R, g, k, c, s); }, s, best, best_ms);
 }
 
 acs_status tune_stencil(const double* u, const double* a, double* out, const Geom& g, const StarCoef& cf,
                         cudaStream_t s, acs_tile* best, float* best_ms) {
+    static const int staging[] = {0, ACS_TILE_TMA};   // element-wise cp.async or TMA plane copies
     return tune_grid(
-        ACS_KIND_STENCIL, g, kStarTiles, 6,
+        ACS_KIND_STENCIL, g, kStarTiles, 6, staging, 2,
         [&](const acs_tile& c) { return launch_stencil_saturated(u, a, out, g, cf, c, s); }, s, best, best_ms);
 }
 
@@ -202,8 +207,11 @@ acs_status tune_cache_load(const char* path) {
             fclose(f);
             return fail(ACS_ERR_INVALID, "autotune cache names an unbuilt tile %dx%d", bx, by);
         }
-        const bool balanced = flags == ACS_TILE_BALANCED && !batch_key;
-        if ((flags != 0 && !balanced) || (!balanced && kc < 1) || (balanced && kc != 0)) {
+        const bool tma_ok = key[0] == '1';   // TMA staging: single-grid star stencil
+        const bool flags_ok = (flags & ~(ACS_TILE_BALANCED | ACS_TILE_TMA)) == 0 &&
+                              (!(flags & ACS_TILE_TMA) || tma_ok) && (!(flags & ACS_TILE_BALANCED) || !batch_key);
+        const bool balanced = (flags & ACS_TILE_BALANCED) != 0;
+        if (!flags_ok || (!balanced && kc < 1) || (balanced && kc != 0)) {
             fclose(f);
             return fail(ACS_ERR_INVALID, "autotune cache line with bad z-chunk %d / flags %d", kc, flags);
         }

@@ -118,7 +118,7 @@ def test_autotune_single_grid_and_cache_roundtrip(tmp_path):
     out = torch.empty((40, 48, 64), dtype=torch.float64, device="cuda")
     tile, ms = binding.acs_autotune_stencil(ud, ad, out)
     assert tile[0] in (16, 32, 64) and tile[1] in (4, 8, 16) and ms > 0
-    assert tile[2] >= 1 or tile[3] == binding.TILE_BALANCED
+    assert tile[2] >= 1 or tile[3] & binding.TILE_BALANCED
     U = inputs.rhs_field(40, 36, 30, halo=2, seed=7501)
     Ud = to_dev(U)
     R = torch.empty((5, 30, 36, 40), dtype=torch.float64, device="cuda")
@@ -149,7 +149,8 @@ def test_autotune_single_grid_and_cache_roundtrip(tmp_path):
     for text in ("acs-tune-cache 1\n48 8 8 1.0 1:8x8x8;\n",          # unbuilt tile
                  "acs-tune-cache 2\n32 8 0 1 1.0 3:8x8x8;\n",        # balanced schedule for a batch
                  "acs-tune-cache 2\n32 8 8 1 1.0 1:8x8x8;\n",        # balanced with a z-chunk
-                 "acs-tune-cache 2\n32 8 8 2 1.0 1:8x8x8;\n",        # unknown flag
+                 "acs-tune-cache 2\n32 8 8 4 1.0 1:8x8x8;\n",        # unknown flag
+                 "acs-tune-cache 2\n32 8 8 2 1.0 0:8x8x8;\n",        # TMA staging for the RHS
                  "acs-tune-cache 3\n"):
         bad = tmp_path / "bad.txt"
         bad.write_text(text)

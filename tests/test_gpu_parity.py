@@ -172,6 +172,32 @@ def test_stencil_balanced_whole_rounds(dims, tile):
     assert_parity(_star_gpu("saturated", u, a, tile=tile).cpu().numpy(), ref, what=f"stencil balanced {dims} {tile}")
 
 
+def test_stencil_tma_staging_layouts_and_no_timeouts():
+    """TMA plane staging (ACS_TILE_TMA) matches the oracle where the layout allows it, and an
+    odd halo or a base 8 bytes past a 16-byte boundary fall back to element-wise staging with
+    results that still match; no bounded wait ran out."""
+    before = binding.acs_wait_timeouts()
+    u, a = inputs.stencil_fields(40, 36, 30, halo=4, seed=4700)
+    ref = oracle.stencil(u, a)
+    tma = (32, 8, 0, binding.TILE_TMA)
+    assert_parity(_star_gpu("saturated", u, a, tile=tma).cpu().numpy(), ref, what="tma")
+    u5, a5 = inputs.stencil_fields(40, 36, 30, halo=5, seed=4701)
+    assert_parity(_star_gpu("saturated", u5, a5, halo=5, tile=tma).cpu().numpy(), oracle.stencil(u5, a5, halo=5),
+                  what="tma requested, halo 5")
+    flat_u = torch.zeros(u.size + 1, dtype=torch.float64, device="cuda")
+    flat_a = torch.zeros(a.size + 1, dtype=torch.float64, device="cuda")
+    uv = flat_u[1:].view(u.shape)
+    av = flat_a[1:].view(a.shape)
+    assert uv.data_ptr() % 16 == 8
+    uv.copy_(torch.from_numpy(u))
+    av.copy_(torch.from_numpy(a))
+    out = torch.full((30, 36, 40), float("nan"), dtype=torch.float64, device="cuda")
+    binding.acs_stencil_saturated(uv, av, out, tile=tma)
+    torch.cuda.synchronize()
+    assert_parity(out.cpu().numpy(), ref, what="tma requested, base 8 bytes off")
+    assert binding.acs_wait_timeouts() == before
+
+
 @pytest.mark.parametrize("form", ["plain", "saturated"])
 def test_stencil_48cubed_full(form):
     u, a = inputs.stencil_fields(48, seed=inputs.SEED_STENCIL)
@@ -181,7 +207,8 @@ def test_stencil_48cubed_full(form):
 
 @pytest.mark.parametrize("dims", [(1, 1, 1), (5, 3, 2), (37, 29, 23), (65, 9, 17), (100, 33, 12)])
 @pytest.mark.parametrize("tile", [None, (32, 4, 3), (64, 8, 0), (16, 16, 5), (64, 4, 1), (32, 16, 2),
-                                  (32, 8, 0, 1), (16, 16, 0, 1), (64, 4, 0, 1)])
+                                  (32, 8, 0, 1), (16, 16, 0, 1), (64, 4, 0, 1),
+                                  (32, 8, 0, 2), (16, 16, 3, 2), (64, 8, 1, 2), (32, 4, 0, 3), (16, 16, 0, 3)])
 def test_stencil_saturated_ragged(dims, tile):
     nx, ny, nz = dims
     u, a = inputs.stencil_fields(nx, ny, nz, seed=4000 + nx + 5 * ny + 11 * nz)
