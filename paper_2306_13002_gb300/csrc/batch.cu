@@ -58,7 +58,7 @@ __device__ __forceinline__ int find_item(const long long* __restrict__ prefix, i
 }
 
 template <int BX, int BY, int KIND>
-__global__ void __launch_bounds__(BX * BY, KIND == ACS_KIND_RHS ? RhsShape<BX, BY>::MINB : 1)
+__global__ void __launch_bounds__(BX * BY, KIND == ACS_KIND_RHS ? RhsShape<BX, BY>::MINB : StarShape<BX, BY>::MINB)
     batch_kernel(const unsigned char* __restrict__ ws, unsigned long long* counter, RhsConst rk, StarCoef sc) {
     extern __shared__ __align__(16) double smem[];
     __shared__ long long s_unit;
