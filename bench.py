@@ -52,8 +52,8 @@ NCU_TRAFFIC = {
     # one-pass ncu captures (dram__bytes_read.sum + dram__bytes_write.sum) of one launch at
     # 256^3, the 4th after 3 warm-ups, in the shapes the autotuner picks; summary in
     # profiles/bench_256_launch_list.md.
-    "fbef47f9269a540c:16x16, balanced": 1410000000 + 643050000,
-    "fbef47f9269a540c:32x8, balanced": 1560000000 + 644120000,
+    "ec75da79f4957a5e:16x16, balanced": 1420000000 + 642890000,
+    "ec75da79f4957a5e:32x8, balanced": 1560000000 + 644230000,
 }
 
 
