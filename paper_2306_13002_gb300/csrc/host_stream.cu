@@ -1,10 +1,12 @@
 // acs_rhs_saturated_host: the saturated RHS on host buffers, streamed through the GPU in
 // z-slabs so that host-to-device copies, kernels and device-to-host copies overlap.
 //
-// The grid is cut into slabs of `slab` interior z-planes. Slab s needs input planes
-// [k0-2, k1+2) and produces output planes [k0, k1). NB input and NB output buffers (in the
-// caller's workspace) rotate between slabs. For slab s > 0 the four halo planes it shares with
-// slab s-1 are copied from the previous input buffer by a small kernel on the upload stream,
+// The grid is cut into slabs of at most `slab` interior z-planes: the first two and the last
+// two slabs are a quarter and a half of `slab` (so that the pipeline fills and drains on small
+// copies), the rest `slab`. Slab s needs input planes [k0-2, k1+2) and produces output planes
+// [k0, k1). NB input and NB output buffers (in the caller's workspace) rotate between slabs.
+// For slab s > 0 the four halo planes it shares with slab s-1 are copied from the previous
+// input buffer by a small kernel on the upload stream,
 // so every input plane crosses the host link once (copy-engine device-to-device copies in this
 // place serialised the two link directions on GB300 and nearly doubled the step time).
 // Library-owned streams per device:
@@ -18,6 +20,7 @@
 // stream, and the caller's stream waits for the last download, so the call behaves like one
 // operation on `stream`. Host buffers should be page-locked for the copies to overlap.
 #include <mutex>
+#include <vector>
 
 #include "acs_internal.cuh"
 
@@ -111,7 +114,24 @@ acs_status rhs_host_run(const double* U, double* R, const Geom& g, const RhsCons
     auto chk = [](cudaError_t e, const char* what) { return e == cudaSuccess ? ACS_OK : launch_status(what); };
     if ((st = chk(cudaEventRecord(ev.entry(), caller), "cudaEventRecord")) != ACS_OK) return st;
     if ((st = chk(cudaStreamWaitEvent(ss->up, ev.entry(), 0), "cudaStreamWaitEvent")) != ACS_OK) return st;
-    const int nslab = (g.nz + slab - 1) / slab;
+    // Slab boundaries: ramp up, full slabs, ramp down.
+    std::vector<int> kb(1, 0);
+    {
+        const int q = slab / 4 > 0 ? slab / 4 : 1, h = slab / 2 > 0 ? slab / 2 : 1;
+        const int ramp = q + h;
+        if (g.nz > 2 * ramp + slab) {
+            kb.push_back(q);
+            kb.push_back(ramp);
+            const int mid_end = g.nz - ramp;
+            for (int k = ramp + slab; k < mid_end; k += slab) kb.push_back(k);
+            kb.push_back(mid_end);
+            kb.push_back(mid_end + h);
+        } else {
+            for (int k = slab; k < g.nz; k += slab) kb.push_back(k);
+        }
+        kb.push_back(g.nz);
+    }
+    const int nslab = (int)kb.size() - 1;
     const size_t b8 = sizeof(double);
     // one strided copy per direction and slab while the pitches fit the 2D copy's limit
     int max_pitch = 0;
@@ -122,14 +142,15 @@ acs_status rhs_host_run(const double* U, double* R, const Geom& g, const RhsCons
                        (double)b8 * (double)in_comp <= (double)max_pitch;
     for (int s = 0; s < nslab; ++s) {
         const int b = s % NB, bp = (s + NB - 1) % NB;
-        const int k0 = s * slab, k1 = (k0 + slab < g.nz) ? k0 + slab : g.nz, kz = k1 - k0;
+        const int k0 = kb[s], k1 = kb[s + 1], kz = k1 - k0;
         cudaStream_t comp = ss->comp[s & 1];
         // 1. upload planes [k0-H, k1+H) of every component into inb[b]
         if (s >= NB && (st = chk(cudaStreamWaitEvent(ss->up, ev.done(b), 0), "cudaStreamWaitEvent")) != ACS_OK)
             return st;
         int first = 0;
         if (s > 0) {   // the 2H planes shared with slab s-1 come from its buffer
-            halo_planes_kernel<<<dim3(64, 5), 256, 0, ss->up>>>(inb[b], inb[bp] + (i64)slab * in_plane,
+            const int kz_prev = k0 - kb[s - 1];   // the shared planes start kz_prev planes into slab s-1
+            halo_planes_kernel<<<dim3(64, 5), 256, 0, ss->up>>>(inb[b], inb[bp] + (i64)kz_prev * in_plane,
                                                                  2 * H * in_plane, in_comp);
             if ((st = launch_status("halo_planes_kernel")) != ACS_OK) return st;
             first = 2 * H;
