@@ -4,11 +4,13 @@
 // shape of the parallelism decides performance (Sec. II-C). Here the shape is ours to
 // choose: the tuner times every built tile (BX x BY) with a few z-chunk lengths and with the
 // balanced one-block-per-slot schedule (single grids), for the star stencil each both with
-// element-wise and with TMA plane staging, on the
-// caller's own buffers (CUDA events on the caller's stream, best of three launches after a
-// warm-up), and records the fastest per workload shape in a process-wide cache. A saturated
-// call with tile == NULL uses the cached shape for its grid size when there is one.
+// element-wise and with TMA plane staging, on the caller's own buffers (CUDA events on the
+// caller's stream, best of three launches after a warm-up); for single grids it re-times the
+// three fastest in turn (median of seven each). The fastest shape per workload shape goes into
+// a process-wide cache, and a saturated call with tile == NULL uses the cached shape for its
+// grid size when there is one.
 // Tuning overwrites the output buffers and synchronises the stream; it cannot be captured.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -72,6 +74,43 @@ acs_status time_best(F run, cudaStream_t s, Timer& t, float& ms) {
     return ACS_OK;
 }
 
+// Second round over the best few candidates of the first: they are timed in turn (A, B, C,
+// A, B, C, ...) so that a drift of the device's clock or temperature during tuning touches
+// them alike, and the lowest median wins.
+template <class Launch>
+acs_status refine(std::vector<std::pair<float, acs_tile>>& ranked, Launch launch, cudaStream_t s, Timer& t,
+                  acs_tile& bt, float& bms) {
+    std::sort(ranked.begin(), ranked.end(), [](const std::pair<float, acs_tile>& x, const std::pair<float, acs_tile>& y) {
+        return x.first < y.first;
+    });
+    const size_t k = ranked.size() < 3 ? ranked.size() : 3;
+    if (k == 0) return ACS_OK;
+    constexpr int kRounds = 7;
+    std::vector<std::vector<float>> times(k);
+    for (int r = 0; r < kRounds; ++r) {
+        for (size_t c = 0; c < k; ++c) {
+            if (cudaEventRecord(t.a, s) != cudaSuccess) return launch_status("cudaEventRecord");
+            acs_status st = launch(ranked[c].second);
+            if (st != ACS_OK) return st;
+            if (cudaEventRecord(t.b, s) != cudaSuccess) return launch_status("cudaEventRecord");
+            if (cudaEventSynchronize(t.b) != cudaSuccess) return launch_status("cudaEventSynchronize");
+            float e = 0.f;
+            if (cudaEventElapsedTime(&e, t.a, t.b) != cudaSuccess) return launch_status("cudaEventElapsedTime");
+            times[c].push_back(e);
+        }
+    }
+    bms = 1e30f;
+    for (size_t c = 0; c < k; ++c) {
+        std::sort(times[c].begin(), times[c].end());
+        const float med = times[c][kRounds / 2];
+        if (med < bms) {
+            bms = med;
+            bt = ranked[c].second;
+        }
+    }
+    return ACS_OK;
+}
+
 template <class Launch>
 acs_status tune_grid(int kind, const Geom& g, const int (*tiles)[2], int ntiles, const int* staging, int nstaging,
                      Launch launch, cudaStream_t s, acs_tile* best, float* best_ms) {
@@ -79,6 +118,7 @@ acs_status tune_grid(int kind, const Geom& g, const int (*tiles)[2], int ntiles,
     if (!t.init()) return launch_status("cudaEventCreate");
     acs_tile bt = {0, 0, 0, 0};
     float bms = 1e30f;
+    std::vector<std::pair<float, acs_tile>> ranked;
     for (int q = 0; q < ntiles; ++q) {
         for (int kc : kChunks) {
             if (kc > g.nz && kc != kChunks[0] && kc != kBalanced) continue;
@@ -88,13 +128,12 @@ acs_status tune_grid(int kind, const Geom& g, const int (*tiles)[2], int ntiles,
                 float ms = 0.f;
                 acs_status st = time_best([&]() { return launch(cand); }, s, t, ms);
                 if (st != ACS_OK) return st;
-                if (ms < bms) {
-                    bms = ms;
-                    bt = cand;
-                }
+                ranked.push_back({ms, cand});
             }
         }
     }
+    acs_status st = refine(ranked, launch, s, t, bt, bms);
+    if (st != ACS_OK) return st;
     {
         std::lock_guard<std::mutex> lk(g_mu);
         g_cache[key_of(kind, &g, 1)] = Entry{bt, bms};
