@@ -6,17 +6,19 @@
 // copies), the rest `slab`. Slab s needs input planes [k0-2, k1+2) and produces output planes
 // [k0, k1). NB input and NB output buffers (in the caller's workspace) rotate between slabs.
 // For slab s > 0 the four halo planes it shares with slab s-1 are copied from the previous
-// input buffer by a small kernel on the upload stream,
-// so every input plane crosses the host link once (copy-engine device-to-device copies in this
-// place serialised the two link directions on GB300 and nearly doubled the step time).
+// input buffer by a small kernel, so every input plane crosses the host link once (copy-engine
+// device-to-device copies in this place serialised the two link directions on GB300 and
+// nearly doubled the step time).
 // Library-owned streams per device:
 //   up        uploads slab s (one strided cudaMemcpy2DAsync over the five components),
+//   halo      copies slab s's shared halo planes (after upload s-1, once buffer s % NB is free),
 //   comp[2]   run the kernel of slab s on comp[s % 2], so the tail of one slab's kernel
 //             overlaps the start of the next,
 //   down      downloads slab s after its kernel (one cudaMemcpy2DAsync).
-// Events order the hand-offs: kernel s after upload s; upload s (reusing buffer s % NB)
-// after kernel s - NB; kernel s (reusing output buffer s % NB) after download s - NB; download
-// s after kernel s. The first upload waits for everything already enqueued on the caller's
+// Events order the hand-offs: kernel s after upload s and halo copy s; upload s and halo copy
+// s (reusing buffer s % NB) after kernel s - NB and halo copy s - NB + 1 (the last readers of
+// that buffer); kernel s (reusing output buffer s % NB) after download s - NB; download s after
+// kernel s. The first upload waits for everything already enqueued on the caller's
 // stream, and the caller's stream waits for the last download, so the call behaves like one
 // operation on `stream`. Host buffers should be page-locked for the copies to overlap.
 #include <mutex>
@@ -39,7 +41,7 @@ __global__ void halo_planes_kernel(double* __restrict__ dst, const double* __res
 }
 
 struct StreamSet {
-    cudaStream_t up = nullptr, down = nullptr, comp[2] = {nullptr, nullptr};
+    cudaStream_t up = nullptr, down = nullptr, halo = nullptr, comp[2] = {nullptr, nullptr};
     bool ok = false;
 };
 std::mutex g_ss_mu;
@@ -54,6 +56,7 @@ acs_status streams_for_device(StreamSet** out) {
     if (!s.ok) {
         if (cudaStreamCreateWithFlags(&s.up, cudaStreamNonBlocking) != cudaSuccess ||
             cudaStreamCreateWithFlags(&s.down, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&s.halo, cudaStreamNonBlocking) != cudaSuccess ||
             cudaStreamCreateWithFlags(&s.comp[0], cudaStreamNonBlocking) != cudaSuccess ||
             cudaStreamCreateWithFlags(&s.comp[1], cudaStreamNonBlocking) != cudaSuccess)
             return launch_status("cudaStreamCreateWithFlags");
@@ -64,7 +67,7 @@ acs_status streams_for_device(StreamSet** out) {
 }
 
 struct Events {
-    static constexpr int N = 3 * NB + 2;
+    static constexpr int N = 4 * NB + 2;
     cudaEvent_t e[N] = {nullptr};
     ~Events() {
         for (auto& x : e)
@@ -80,6 +83,7 @@ struct Events {
     cudaEvent_t down(int b) { return e[2 * NB + b]; }
     cudaEvent_t entry() { return e[3 * NB]; }
     cudaEvent_t exit() { return e[3 * NB + 1]; }
+    cudaEvent_t halo(int b) { return e[3 * NB + 2 + b]; }
 };
 
 }  // namespace
@@ -147,14 +151,11 @@ acs_status rhs_host_run(const double* U, double* R, const Geom& g, const RhsCons
         // 1. upload planes [k0-H, k1+H) of every component into inb[b]
         if (s >= NB && (st = chk(cudaStreamWaitEvent(ss->up, ev.done(b), 0), "cudaStreamWaitEvent")) != ACS_OK)
             return st;
-        int first = 0;
-        if (s > 0) {   // the 2H planes shared with slab s-1 come from its buffer
-            const int kz_prev = k0 - kb[s - 1];   // the shared planes start kz_prev planes into slab s-1
-            halo_planes_kernel<<<dim3(64, 5), 256, 0, ss->up>>>(inb[b], inb[bp] + (i64)kz_prev * in_plane,
-                                                                 2 * H * in_plane, in_comp);
-            if ((st = launch_status("halo_planes_kernel")) != ACS_OK) return st;
-            first = 2 * H;
-        }
+        // buffer b's previous slab (s - NB) is also read by halo copy s - NB + 1
+        if (s >= NB &&
+            (st = chk(cudaStreamWaitEvent(ss->up, ev.halo((s - NB + 1) % NB), 0), "cudaStreamWaitEvent")) != ACS_OK)
+            return st;
+        const int first = s > 0 ? 2 * H : 0;
         const size_t up_bytes = b8 * (size_t)(kz + 2 * H - first) * in_plane;
         if (use2d) {
             if ((st = chk(cudaMemcpy2DAsync(inb[b] + (i64)first * in_plane, b8 * in_comp,
@@ -171,8 +172,22 @@ acs_status rhs_host_run(const double* U, double* R, const Geom& g, const RhsCons
                     return st;
         }
         if ((st = chk(cudaEventRecord(ev.up(b), ss->up), "cudaEventRecord")) != ACS_OK) return st;
+        // 1b. the 2H planes shared with slab s-1 come from its buffer, copied by a small kernel on
+        //     the halo stream (after upload s-1 and once buffer b is free), so that the uploads
+        //     never queue behind a kernel waiting for SMs.
+        if (s > 0) {
+            if ((st = chk(cudaStreamWaitEvent(ss->halo, ev.up(bp), 0), "cudaStreamWaitEvent")) != ACS_OK) return st;
+            if (s >= NB && (st = chk(cudaStreamWaitEvent(ss->halo, ev.done(b), 0), "cudaStreamWaitEvent")) != ACS_OK)
+                return st;
+            const int kz_prev = k0 - kb[s - 1];   // the shared planes start kz_prev planes into slab s-1
+            halo_planes_kernel<<<dim3(64, 5), 256, 0, ss->halo>>>(inb[b], inb[bp] + (i64)kz_prev * in_plane,
+                                                                   2 * H * in_plane, in_comp);
+            if ((st = launch_status("halo_planes_kernel")) != ACS_OK) return st;
+            if ((st = chk(cudaEventRecord(ev.halo(b), ss->halo), "cudaEventRecord")) != ACS_OK) return st;
+        }
         // 2. kernel of slab s
         if ((st = chk(cudaStreamWaitEvent(comp, ev.up(b), 0), "cudaStreamWaitEvent")) != ACS_OK) return st;
+        if (s > 0 && (st = chk(cudaStreamWaitEvent(comp, ev.halo(b), 0), "cudaStreamWaitEvent")) != ACS_OK) return st;
         if (s >= NB && (st = chk(cudaStreamWaitEvent(comp, ev.down(b), 0), "cudaStreamWaitEvent")) != ACS_OK)
             return st;
         Geom sg = g;
