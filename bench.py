@@ -124,10 +124,11 @@ class ClockSampler:
 
 
 def tile_text(tile) -> str:
-    """'32x8, z-chunk 16' or '16x16, balanced' for an (bx, by, kchunk[, flags]) tuple."""
+    """'32x8, z-chunk 16' or '16x16, balanced, TMA' for an (bx, by, kchunk[, flags]) tuple."""
     from paper_2306_13002_gb300 import binding
     bx, by, kc, flags = (tuple(tile) + (0, 0, 0, 0))[:4]
-    return f"{bx}x{by}, " + ("balanced" if flags & binding.TILE_BALANCED else f"z-chunk {kc}")
+    text = f"{bx}x{by}, " + ("balanced" if flags & binding.TILE_BALANCED else f"z-chunk {kc}")
+    return text + (", TMA" if flags & binding.TILE_TMA else "")
 
 
 def cpu_baseline(U: np.ndarray, budget_s: float = 10.0) -> dict:

@@ -124,10 +124,10 @@ typedef struct acs_tile {
 #define ACS_TILE_BALANCED 1
 /* acs_tile.flags: stage each xy-plane of the input into shared memory with one tensor copy
  * (TMA, cp.async.bulk.tensor) completing on an mbarrier, instead of element-wise cp.async.
- * Built for acs_stencil_saturated (and its autotuner); ACS_ERR_UNSUPPORTED from the other
- * entry points. Used where the layout allows it (16-byte aligned input, row and plane strides
- * that are multiples of 2 elements, even halo); other layouts are staged element-wise, with
- * the same results. Waits on the mbarriers are bounded (about one second); one that runs out
+ * Accepted by the single-grid saturated calls and their autotuners (the batch entry points
+ * reject it). Used where the layout allows it (16-byte aligned input, row, plane and component
+ * strides that are multiples of 2 elements, even halo); other layouts are staged element-wise,
+ * with the same results. Waits on the mbarriers are bounded (about one second); one that runs out
  * is counted (acs_wait_timeouts) and the call's results are then wrong, but the kernel ends. */
 #define ACS_TILE_TMA 2
 
@@ -148,7 +148,8 @@ acs_status acs_rhs_plain(const double *U, double *R, const acs_grid *g, const ac
  * sum(U at +-2) - 4 sum(U at +-1) + 18 U, FMA throughout, and every plane of U staged in
  * shared memory ahead of the arithmetic (bulk load). Same arguments as acs_rhs_plain plus
  *   tile   launch shape or NULL (the autotuned shape for this grid size if acs_autotune_rhs
- *          recorded one, else 16 x 16 with the balanced schedule).
+ *          recorded one, else 16 x 16 with the balanced schedule and TMA plane staging where
+ *          the layout allows it).
  */
 acs_status acs_rhs_saturated(const double *U, double *R, const acs_grid *g, const acs_rhs_params *p,
                              const acs_tile *tile, acs_stream stream);
@@ -159,7 +160,7 @@ acs_status acs_rhs_saturated(const double *U, double *R, const acs_grid *g, cons
  *   U, R   host arrays in compact layout (in_sy = nx + 2 halo, in_sz = in_sy (ny + 2 halo),
  *          out_sy = nx, out_sz = nx ny; component strides free). Page-locked memory is
  *          needed for the copies to overlap; pageable memory works but serialises.
- *   tile   launch shape of the slab kernels or NULL (16 x 16, balanced schedule).
+ *   tile   launch shape of the slab kernels or NULL (16 x 16, balanced schedule, TMA staging).
  *   ws     device workspace of acs_rhs_host_workspace_bytes(g, slab) bytes (three input and
  *          three output slab buffers), 16-byte aligned.
  * Uploads, the slab kernels (alternating between two streams) and downloads run on four

@@ -310,7 +310,7 @@ acs_status batch_params(int kind, const void* params, RhsConst& rk, StarCoef& sc
     return star_coef(static_cast<const double*>(params), sc);
 }
 
-const acs_tile kDefaultRhsTile = {16, 16, 0, ACS_TILE_BALANCED};
+const acs_tile kDefaultRhsTile = {16, 16, 0, ACS_TILE_BALANCED | ACS_TILE_TMA};
 const acs_tile kDefaultStarTile = {32, 8, 0, ACS_TILE_TMA};
 
 acs_status check_tile(const acs_tile* t, const acs_tile& def, bool (*supported)(int, int), acs_tile& out,
@@ -318,8 +318,6 @@ acs_status check_tile(const acs_tile* t, const acs_tile& def, bool (*supported)(
     out = t ? *t : def;
     if (!t && g && tuned_tile(kind, *g, &out)) return ACS_OK;
     if (out.flags & ~(ACS_TILE_BALANCED | ACS_TILE_TMA)) return fail(ACS_ERR_INVALID, "unknown tile flags 0x%x", out.flags);
-    if ((out.flags & ACS_TILE_TMA) && kind != ACS_KIND_STENCIL)
-        return fail(ACS_ERR_UNSUPPORTED, "TMA plane staging is built for the star stencil");
     if (out.kchunk < 0) return fail(ACS_ERR_INVALID, "kchunk must be >= 0");
     if (!supported(out.bx, out.by)) return fail(ACS_ERR_UNSUPPORTED, "tile %dx%d is not built", out.bx, out.by);
     return ACS_OK;

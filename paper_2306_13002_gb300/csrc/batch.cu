@@ -60,7 +60,7 @@ __device__ __forceinline__ int find_item(const long long* __restrict__ prefix, i
 template <int BX, int BY, int KIND>
 __global__ void __launch_bounds__(BX * BY, KIND == ACS_KIND_RHS ? RhsShape<BX, BY>::MINB : StarShape<BX, BY>::MINB)
     batch_kernel(const unsigned char* __restrict__ ws, unsigned long long* counter, RhsConst rk, StarCoef sc) {
-    extern __shared__ __align__(16) double smem[];
+    extern __shared__ __align__(128) double smem[];
     __shared__ long long s_unit;
     const BatchHeader* h = reinterpret_cast<const BatchHeader*>(ws);
     const BatchDesc* items = reinterpret_cast<const BatchDesc*>(ws + kHeader);
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(BX * BY, KIND == ACS_KIND_RHS ? RhsShape<BX, B
         const int k0 = kc * kchunk;
         const int k1 = min(k0 + kchunk, d.g.nz);
         if (KIND == ACS_KIND_RHS)
-            rhs_march<BX, BY>(d.in0, d.out, d.g, rk, tx * BX, ty * BY, k0, k1, smem);
+            rhs_march<BX, BY, false>(d.in0, d.out, d.g, rk, tx * BX, ty * BY, k0, k1, smem, nullptr, nullptr);
         else
             star_march<BX, BY, false>(d.in0, d.in1, d.out, d.g, sc, tx * BX, ty * BY, k0, k1, smem, nullptr, nullptr);
     }

@@ -15,10 +15,12 @@ struct RhsShape {
     static constexpr int FX_ELEMS = 4 * BY * (BX + 2);
     static constexpr int FY_ELEMS = 4 * (BY + 2) * BX;
     static constexpr int CONST_ELEMS = 16;   // staged constants (RhsRegs)
-    static constexpr size_t BYTES = sizeof(double) * (size_t)(U_ELEMS + FX_ELEMS + FY_ELEMS + CONST_ELEMS);
+    // U ring, flux planes, staged constants, one mbarrier per slot (TMA staging).
+    static constexpr size_t BYTES = sizeof(double) * (size_t)(U_ELEMS + FX_ELEMS + FY_ELEMS + CONST_ELEMS + NSLOT);
     static constexpr int NT = BX * BY;
     static constexpr int MINB = NT <= 256 ? 2 : 1;
     static_assert(NT >= 2 * (BX + BY) && (2 * BX) % 32 == 0, "flux ring needs 2(BX+BY) threads, y-ring whole warps");
+    static_assert((5 * PLANE * sizeof(double)) % 128 == 0, "every ring slot 128-byte aligned");
 };
 
 // The constants of the RHS march as register values: the folded coefficients and Pipe, and
@@ -78,28 +80,69 @@ __device__ __forceinline__ void load_plane(double* slot, const double* __restric
 
 // One block's work: the BX x BY column tile at (i0, j0), z-planes [k0, k1). Ends with all
 // threads past a barrier after their last shared-memory read, so the caller may reuse smem.
-template <int BX, int BY>
+//
+// Plane staging: with TMA = false every thread copies its share of a plane (five components)
+// element by element (cp.async); with TMA = true thread 0 copies the (BX+4) x (BY+4) x 5 box of
+// plane q with one tensor copy (`map`: the 4D tensor map of U, components outermost) that
+// completes on the slot's mbarrier, and the readers wait on it (bounded; timeouts counted in
+// *tmo). Plane q is fill number n = (q - k0 + 2) / 5 of its slot: phase parity n & 1.
+template <int BX, int BY, bool TMA>
 __device__ __forceinline__ void rhs_march(const double* __restrict__ U, double* __restrict__ R, const Geom& g,
-                                          const RhsConst& kc, int i0, int j0, int k0, int k1, double* smem) {
+                                          const RhsConst& kc, int i0, int j0, int k0, int k1, double* smem,
+                                          const CUtensorMap* map, unsigned* tmo) {
     using S = RhsShape<BX, BY>;
     constexpr int PX = S::PX, PLANE = S::PLANE;
+    constexpr unsigned kSlotBytes = 5 * PLANE * sizeof(double);
     double* Us = smem;
     double* Fxs = smem + S::U_ELEMS;
     double* Fys = Fxs + S::FX_ELEMS;
     double* Cs = Fys + S::FY_ELEMS;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(Cs + S::CONST_ELEMS);
     static_assert(sizeof(RhsRegs) <= S::CONST_ELEMS * sizeof(double), "constant staging area");
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
     const int i = i0 + tx, j = j0 + ty;
     const bool active = (i < g.nx) && (j < g.ny);
     const int own = (ty + 2) * PX + (tx + 2);
-    auto slot = [&](int q) -> double* { return Us + ((q + S::NSLOT) % S::NSLOT) * (5 * PLANE); };
+    auto sidx = [&](int q) -> int { return (q + S::NSLOT) % S::NSLOT; };
+    auto slot = [&](int q) -> double* { return Us + sidx(q) * (5 * PLANE); };
+    auto parity = [&](int q) -> unsigned { return (unsigned)((q - k0 + 2) / S::NSLOT) & 1u; };
+    auto issue = [&](int q) {   // thread 0 only
+        uint64_t* bar = bars + sidx(q);
+        mbar_arrive_expect_tx(bar, kSlotBytes);
+        tma_load_4d(slot(q), map, bar, i0 - 2 + g.halo, j0 - 2 + g.halo, q + g.halo, 0);
+    };
+    // this thread's waits have all completed; a ring that is not 128-byte aligned (the kernels
+    // declare their shared memory so) is counted and staged by nobody, never copied into
+    bool ok = true;
+    int lost = 0x7fffffff;                   // the plane whose wait ran out
+    if (TMA && (smem_addr(Us) & 127u) != 0) {
+        ok = false;
+        if (tid == 0) atomicAdd(tmo, 1u);
+    }
+    auto wait_plane = [&](int q) {
+        if (ok && !mbar_wait_bounded(bars + sidx(q), parity(q), tmo)) {
+            ok = false;
+            lost = q;
+        }
+    };
 
     // Prologue: planes k0-2 .. k0+2, and the constants into registers.
     stage_consts_write(Cs, RhsRegs{kc, -4.0, 18.0}, tid);
-    for (int q = k0 - 2; q <= k0 + 2; ++q) load_plane<BX, BY>(slot(q), U, g, i0, j0, q, tid);
-    cp_async_commit();
-    cp_async_wait_all();
+    if (TMA) {
+        if (tid == 0) {
+            for (int s = 0; s < S::NSLOT; ++s) mbar_init(bars + s, 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+        if (tid == 0 && ok)
+            for (int q = k0 - 2; q <= k0 + 2; ++q) issue(q);
+        for (int q = k0 - 2; q <= k0 + 2; ++q) wait_plane(q);
+    } else {
+        for (int q = k0 - 2; q <= k0 + 2; ++q) load_plane<BX, BY>(slot(q), U, g, i0, j0, q, tid);
+        cp_async_commit();
+        cp_async_wait_all();
+    }
     __syncthreads();
     const RhsRegs kr = stage_consts_read<RhsRegs>(Cs);
     const RhsConst& k = kr.k;
@@ -146,7 +189,10 @@ __device__ __forceinline__ void rhs_march(const double* __restrict__ U, double* 
             point_flux(s[own], s[PLANE + own], s[2 * PLANE + own], s[3 * PLANE + own], s[4 * PLANE + own], k, pfx, pfy,
                        fzp);
         }
-        cp_async_wait_all();  // plane kk+2 (issued one step earlier) has landed
+        if (TMA)
+            wait_plane(kk + 2);   // plane kk+2 (issued one step earlier) has landed
+        else
+            cp_async_wait_all();
         __syncthreads();
 
         // (3) the right-hand side at plane kk.
@@ -191,10 +237,26 @@ __device__ __forceinline__ void rhs_march(const double* __restrict__ U, double* 
         }
         __syncthreads();  // slot kk-2 and the flux planes are free again
         // (5) bulk-load plane kk+3 into the slot of kk-2.
-        if (kk + 3 <= k1 + 1) load_plane<BX, BY>(slot(kk + 3), U, g, i0, j0, kk + 3, tid);
-        cp_async_commit();
+        if (TMA) {
+            if (kk + 3 <= k1 + 1 && tid == 0 && ok) {
+                fence_proxy_async();
+                issue(kk + 3);
+            }
+        } else {
+            if (kk + 3 <= k1 + 1) load_plane<BX, BY>(slot(kk + 3), U, g, i0, j0, kk + 3, tid);
+            cp_async_commit();
+        }
     }
-    cp_async_wait_all();
+    if (TMA) {
+        // A copy whose wait ran out may still be in flight: give it one more bounded wait
+        // before the slots are reused or the block exits. Then retire the barriers.
+        if (tid == 0 && !ok && lost != 0x7fffffff) mbar_wait_bounded(bars + sidx(lost), parity(lost), tmo);
+        __syncthreads();
+        if (tid == 0)
+            for (int s = 0; s < S::NSLOT; ++s) mbar_inval(bars + s);
+    } else {
+        cp_async_wait_all();
+    }
 }
 
 template <int BX, int BY>
@@ -202,8 +264,8 @@ struct StarShape {
     static constexpr int PX = BX + 8, PY = BY + 8, PLANE = PX * PY;
     static constexpr int NSLOT = 10;
     static constexpr int CONST_ELEMS = 16;   // staged StarCoef
-    // Ring, staged constants, one mbarrier per slot (TMA staging), and 128 bytes to align the
-    // ring for TMA.
+    // Ring, staged constants, one mbarrier per slot (TMA staging), and 128 bytes to round the
+    // ring's base up to a 128-byte boundary.
     static constexpr size_t BYTES = sizeof(double) * ((size_t)NSLOT * PLANE + CONST_ELEMS + NSLOT) + 128;
     static constexpr int NT = BX * BY;
     // Blocks per SM the launch bounds ask registers for: 2048 threads per SM at most (and the
@@ -242,6 +304,8 @@ __device__ __forceinline__ void star_march(const double* __restrict__ u, const d
     using S = StarShape<BX, BY>;
     constexpr int PX = S::PX, PLANE = S::PLANE;
     constexpr unsigned kPlaneBytes = PLANE * sizeof(double);
+    // The ring's base rounded up to 128 bytes (a TMA destination must be). This also measured
+    // faster for the element-wise staging than addressing the declared base directly.
     double* smem = align128(smem_raw);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
     const int i = i0 + tx, j = j0 + ty;
@@ -335,7 +399,7 @@ __device__ __forceinline__ void star_march(const double* __restrict__ u, const d
     if (TMA) {
         // A copy whose wait ran out may still be in flight: give it one more bounded wait
         // before the slots are reused or the block exits. Then retire the barriers.
-        if (tid == 0 && !ok) mbar_wait_bounded(bars + sidx(lost), parity(lost), tmo);
+        if (tid == 0 && !ok && lost != 0x7fffffff) mbar_wait_bounded(bars + sidx(lost), parity(lost), tmo);
         __syncthreads();
         if (tid == 0)
             for (int s = 0; s < S::NSLOT; ++s) mbar_inval(bars + s);

@@ -18,24 +18,29 @@
 //  * Every add, subtract and multiply is issued as an FMA (see Pipe in acs_internal.cuh):
 //    on GB300 DFMA issues faster than DADD/DMUL, and the results are bit-identical.
 //  * Bulk load (Sec. VI-B): each xy-plane of U, with a 2-cell halo, is copied into a ring
-//    of five shared-memory slots with cp.async one step ahead of its use, so every load
+//    of five shared-memory slots one step ahead of its use (element-wise with cp.async, or
+//    with ACS_TILE_TMA as one tensor copy per plane completing on an mbarrier), so every load
 //    of the body is issued before the arithmetic that consumes it.
 //
 // Block: BX x BY threads own a BX x BY column tile and march z over [k0, k1).
 // Shared memory: U ring [5 slots][5 comps][BY+4][BX+4], F_x [4][BY][BX+2] (x from -1 to
 // BX), F_y [4][BY+2][BX] (y from -1 to BY). The x/y ring of fluxes just outside the tile
 // is computed by the first 2(BX+BY) threads.
+#include <cstring>
+
 #include "march.cuh"
 
 namespace acs {
 namespace {
 
-template <int BX, int BY>
+template <int BX, int BY, bool TMA>
 __global__ void __launch_bounds__(BX * BY, RhsShape<BX, BY>::MINB)
-    rhs_saturated_kernel(const double* __restrict__ U, double* __restrict__ R, Geom g, RhsConst k, int kchunk) {
-    extern __shared__ __align__(16) double smem[];
+    rhs_saturated_kernel(const double* __restrict__ U, double* __restrict__ R, Geom g, RhsConst k, int kchunk,
+                         const __grid_constant__ CUtensorMap map, unsigned* tmo) {
+    extern __shared__ __align__(128) double smem[];
     const int k0 = blockIdx.z * kchunk;
-    rhs_march<BX, BY>(U, R, g, k, blockIdx.x * BX, blockIdx.y * BY, k0, min(k0 + kchunk, g.nz), smem);
+    rhs_march<BX, BY, TMA>(U, R, g, k, blockIdx.x * BX, blockIdx.y * BY, k0, min(k0 + kchunk, g.nz), smem, &map,
+                           tmo);
 }
 
 // Balanced schedule (ACS_TILE_BALANCED): one block per resident slot. The work is the list
@@ -48,10 +53,11 @@ __global__ void __launch_bounds__(BX * BY, RhsShape<BX, BY>::MINB)
 // from DRAM again (about 2x the input bytes); a variant that kept all blocks at the same z
 // (whole-column rounds, then base/top shares) read 1.18x the input but ran 0.3-1.4 % slower
 // on GB300, and this kernel is bound by the FP64 pipe, not by DRAM.
-template <int BX, int BY>
+template <int BX, int BY, bool TMA>
 __global__ void __launch_bounds__(BX * BY, RhsShape<BX, BY>::MINB)
-    rhs_saturated_balanced_kernel(const double* __restrict__ U, double* __restrict__ R, Geom g, RhsConst k) {
-    extern __shared__ __align__(16) double smem[];
+    rhs_saturated_balanced_kernel(const double* __restrict__ U, double* __restrict__ R, Geom g, RhsConst k,
+                                  const __grid_constant__ CUtensorMap map, unsigned* tmo) {
+    extern __shared__ __align__(128) double smem[];
     const int ntx = (g.nx + BX - 1) / BX;
     const i64 W = (i64)ntx * ((g.ny + BY - 1) / BY) * g.nz;
     i64 L = W * blockIdx.x / gridDim.x;
@@ -60,31 +66,30 @@ __global__ void __launch_bounds__(BX * BY, RhsShape<BX, BY>::MINB)
         const i64 col = L / g.nz;
         const int z0 = (int)(L - col * g.nz);
         const int z1 = (int)min((i64)g.nz, z0 + (L1 - L));
-        rhs_march<BX, BY>(U, R, g, k, (int)(col % ntx) * BX, (int)(col / ntx) * BY, z0, z1, smem);
+        rhs_march<BX, BY, TMA>(U, R, g, k, (int)(col % ntx) * BX, (int)(col / ntx) * BY, z0, z1, smem, &map, tmo);
         L += z1 - z0;
     }
 }
 
-template <int BX, int BY>
-acs_status launch_balanced(const double* U, double* R, const Geom& g, const RhsConst& k, cudaStream_t s) {
+template <int BX, int BY, bool TMA>
+acs_status launch_tt(const double* U, double* R, const Geom& g, const RhsConst& k, int kchunk, int flags,
+                     const CUtensorMap& map, cudaStream_t s) {
     using S = RhsShape<BX, BY>;
-    const void* fn = (const void*)rhs_saturated_balanced_kernel<BX, BY>;
-    acs_status st = ensure_smem(fn, S::BYTES);
-    if (st != ACS_OK) return st;
-    const i64 W = (i64)((g.nx + BX - 1) / BX) * ((g.ny + BY - 1) / BY) * g.nz;
-    i64 G = resident_blocks(fn, S::NT, S::BYTES);
-    if (G <= 0) return fail(ACS_ERR_CUDA, "occupancy query failed for rhs_saturated_balanced_kernel");
-    if (G > W) G = W;
-    rhs_saturated_balanced_kernel<BX, BY><<<(unsigned)G, dim3(BX, BY, 1), S::BYTES, s>>>(U, R, g, k);
-    return launch_status("rhs_saturated_balanced_kernel");
-}
-
-template <int BX, int BY>
-acs_status launch_t(const double* U, double* R, const Geom& g, const RhsConst& k, int kchunk, int flags,
-                    cudaStream_t s) {
-    using S = RhsShape<BX, BY>;
-    if (flags & ACS_TILE_BALANCED) return launch_balanced<BX, BY>(U, R, g, k, s);
-    const void* fn = (const void*)rhs_saturated_kernel<BX, BY>;
+    unsigned* tmo = wait_timeout_counter();
+    if (!tmo) return fail(ACS_ERR_CUDA, "cannot address the wait-timeout counter");
+    if (flags & ACS_TILE_BALANCED) {
+        const void* fn = (const void*)rhs_saturated_balanced_kernel<BX, BY, TMA>;
+        acs_status st = ensure_smem(fn, S::BYTES);
+        if (st != ACS_OK) return st;
+        const i64 W = (i64)((g.nx + BX - 1) / BX) * ((g.ny + BY - 1) / BY) * g.nz;
+        i64 G = resident_blocks(fn, S::NT, S::BYTES);
+        if (G <= 0) return fail(ACS_ERR_CUDA, "occupancy query failed for rhs_saturated_balanced_kernel");
+        if (G > W) G = W;
+        rhs_saturated_balanced_kernel<BX, BY, TMA><<<(unsigned)G, dim3(BX, BY, 1), S::BYTES, s>>>(U, R, g, k, map,
+                                                                                                 tmo);
+        return launch_status("rhs_saturated_balanced_kernel");
+    }
+    const void* fn = (const void*)rhs_saturated_kernel<BX, BY, TMA>;
     acs_status st = ensure_smem(fn, S::BYTES);
     if (st != ACS_OK) return st;
     if (kchunk <= 0) {
@@ -93,8 +98,20 @@ acs_status launch_t(const double* U, double* R, const Geom& g, const RhsConst& k
     }
     dim3 block(BX, BY, 1);
     dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, (g.nz + kchunk - 1) / kchunk);
-    rhs_saturated_kernel<BX, BY><<<grid, block, S::BYTES, s>>>(U, R, g, k, kchunk);
+    rhs_saturated_kernel<BX, BY, TMA><<<grid, block, S::BYTES, s>>>(U, R, g, k, kchunk, map, tmo);
     return launch_status("rhs_saturated_kernel");
+}
+
+template <int BX, int BY>
+acs_status launch_t(const double* U, double* R, const Geom& g, const RhsConst& k, int kchunk, int flags,
+                    cudaStream_t s) {
+    CUtensorMap map;
+    memset(&map, 0, sizeof(map));
+    // TMA staging where the layout allows it (the box: the tile plus its 2-cell halo, one
+    // plane, all five components of the halo-extended U); element-wise staging otherwise.
+    if ((flags & ACS_TILE_TMA) && encode_plane_map(U, g, 5, BX + 4, BY + 4, &map) == ACS_OK)
+        return launch_tt<BX, BY, true>(U, R, g, k, kchunk, flags, map, s);
+    return launch_tt<BX, BY, false>(U, R, g, k, kchunk, flags, map, s);
 }
 
 }  // namespace

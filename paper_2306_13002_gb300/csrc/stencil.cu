@@ -48,7 +48,7 @@ template <int BX, int BY, bool TMA>
 __global__ void __launch_bounds__(BX * BY, StarShape<BX, BY>::MINB)
     star_saturated_kernel(const double* __restrict__ u, const double* __restrict__ a, double* __restrict__ out,
                           Geom g, StarCoef cf, int kchunk, const __grid_constant__ CUtensorMap map, unsigned* tmo) {
-    extern __shared__ __align__(16) double smem[];
+    extern __shared__ __align__(128) double smem[];
     const int k0 = blockIdx.z * kchunk;
     star_march<BX, BY, TMA>(u, a, out, g, cf, blockIdx.x * BX, blockIdx.y * BY, k0, min(k0 + kchunk, g.nz), smem,
                             &map, tmo);
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(BX * BY, StarShape<BX, BY>::MINB)
     star_saturated_balanced_kernel(const double* __restrict__ u, const double* __restrict__ a,
                                    double* __restrict__ out, Geom g, StarCoef cf,
                                    const __grid_constant__ CUtensorMap map, unsigned* tmo) {
-    extern __shared__ __align__(16) double smem[];
+    extern __shared__ __align__(128) double smem[];
     const int ntx = (g.nx + BX - 1) / BX;
     const i64 W = (i64)ntx * ((g.ny + BY - 1) / BY) * g.nz;
     i64 L = W * blockIdx.x / gridDim.x;

@@ -85,7 +85,8 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
-// Rounds a dynamic shared-memory pointer up to 128 bytes (the TMA destination alignment).
+// Rounds a dynamic shared-memory pointer up to 128 bytes (the TMA destination alignment); the
+// shape that uses it reserves 128 extra bytes.
 __device__ __forceinline__ double* align128(double* p) {
     const uintptr_t a = (reinterpret_cast<uintptr_t>(p) + 127) & ~static_cast<uintptr_t>(127);
     return reinterpret_cast<double*>(a);

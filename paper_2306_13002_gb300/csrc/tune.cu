@@ -3,8 +3,8 @@
 // The paper leaves the parallel structure to the directive compiler and notes that the
 // shape of the parallelism decides performance (Sec. II-C). Here the shape is ours to
 // choose: the tuner times every built tile (BX x BY) with a few z-chunk lengths and with the
-// balanced one-block-per-slot schedule (single grids), for the star stencil each both with
-// element-wise and with TMA plane staging, on the caller's own buffers (CUDA events on the
+// balanced one-block-per-slot schedule (single grids), each both with element-wise and with
+// TMA plane staging (single grids), on the caller's own buffers (CUDA events on the
 // caller's stream, best of three launches after a warm-up); for single grids it re-times the
 // three fastest in turn (median of seven each). The fastest shape per workload shape goes into
 // a process-wide cache, and a saturated call with tile == NULL uses the cached shape for its
@@ -155,9 +155,9 @@ bool tuned_tile(int kind, const Geom& g, acs_tile* t) {
 
 acs_status tune_rhs(const double* U, double* R, const Geom& g, const RhsConst& k, cudaStream_t s, acs_tile* best,
                     float* best_ms) {
-    static const int staging[] = {0};
+    static const int staging[] = {0, ACS_TILE_TMA};   // element-wise cp.async or TMA plane copies
     return tune_grid(
-        ACS_KIND_RHS, g, kRhsTiles, 6, staging, 1,
+        ACS_KIND_RHS, g, kRhsTiles, 6, staging, 2,
         [&](const acs_tile& c) { return launch_rhs_saturated(U, R, g, k, c, s); }, s, best, best_ms);
 }
 
@@ -246,7 +246,7 @@ acs_status tune_cache_load(const char* path) {
             fclose(f);
             return fail(ACS_ERR_INVALID, "autotune cache names an unbuilt tile %dx%d", bx, by);
         }
-        const bool tma_ok = key[0] == '1';   // TMA staging: single-grid star stencil
+        const bool tma_ok = !batch_key;   // TMA staging: single-grid calls
         const bool flags_ok = (flags & ~(ACS_TILE_BALANCED | ACS_TILE_TMA)) == 0 &&
                               (!(flags & ACS_TILE_TMA) || tma_ok) && (!(flags & ACS_TILE_BALANCED) || !batch_key);
         const bool balanced = (flags & ACS_TILE_BALANCED) != 0;

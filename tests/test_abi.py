@@ -95,8 +95,6 @@ def test_saturated_rejects_unbuilt_tile_and_flags(lib):
     assert _call_rhs(lib, FAKE_U, FAKE_R, _grid(), _params(), sat=True, tile=(24, 8, 0, 0)) == 4
     assert _call_rhs(lib, FAKE_U, FAKE_R, _grid(), _params(), sat=True, tile=(32, 8, 0, 4)) == 1   # unknown flag
     assert _call_rhs(lib, FAKE_U, FAKE_R, _grid(), _params(), sat=True, tile=(32, 8, 0, 5)) == 1
-    # TMA plane staging is built for the star stencil only
-    assert _call_rhs(lib, FAKE_U, FAKE_R, _grid(), _params(), sat=True, tile=(32, 8, 0, binding.TILE_TMA)) == 4
     assert _call_rhs(lib, FAKE_U, FAKE_R, _grid(), _params(), sat=True, tile=(32, 8, -1, 0)) == 1
 
 

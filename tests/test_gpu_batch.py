@@ -150,7 +150,7 @@ def test_autotune_single_grid_and_cache_roundtrip(tmp_path):
                  "acs-tune-cache 2\n32 8 0 1 1.0 3:8x8x8;\n",        # balanced schedule for a batch
                  "acs-tune-cache 2\n32 8 8 1 1.0 1:8x8x8;\n",        # balanced with a z-chunk
                  "acs-tune-cache 2\n32 8 8 4 1.0 1:8x8x8;\n",        # unknown flag
-                 "acs-tune-cache 2\n32 8 8 2 1.0 0:8x8x8;\n",        # TMA staging for the RHS
+                 "acs-tune-cache 2\n32 8 8 2 1.0 2:8x8x8;\n",        # TMA staging for a batch
                  "acs-tune-cache 3\n"):
         bad = tmp_path / "bad.txt"
         bad.write_text(text)

@@ -54,7 +54,8 @@ def test_rhs_32cubed_full(form):
 
 @pytest.mark.parametrize("dims", [(1, 1, 1), (3, 5, 2), (37, 29, 23), (33, 9, 17), (64, 8, 5), (70, 21, 40)])
 @pytest.mark.parametrize("tile", [None, (16, 8, 3), (32, 4, 1), (64, 4, 7), (32, 16, 0), (16, 16, 2),
-                                  (32, 8, 0, 1), (16, 16, 0, 1), (64, 4, 0, 1)])
+                                  (32, 8, 0, 1), (16, 16, 0, 1), (64, 4, 0, 1),
+                                  (32, 8, 0, 2), (16, 16, 3, 2), (16, 8, 1, 2), (16, 16, 0, 3), (32, 4, 0, 3)])
 def test_rhs_saturated_ragged(dims, tile):
     nx, ny, nz = dims
     U = inputs.rhs_field(nx, ny, nz, halo=2, seed=1000 + nx * 7 + ny * 3 + nz)
@@ -63,7 +64,8 @@ def test_rhs_saturated_ragged(dims, tile):
     assert_parity(R, ref, what=f"rhs saturated {dims} tile {tile}")
 
 
-@pytest.mark.parametrize("dims,tile", [((288, 288, 5), (16, 16, 0, 1)), ((288, 290, 4), (32, 8, 0, 1))])
+@pytest.mark.parametrize("dims,tile", [((288, 288, 5), (16, 16, 0, 1)), ((288, 290, 4), (32, 8, 0, 1)),
+                                       ((288, 288, 5), (16, 16, 0, 3))])
 def test_rhs_balanced_whole_rounds(dims, tile):
     """More column tiles than resident blocks (324 > 2 x 152): balanced shares that span
     several whole columns."""
