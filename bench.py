@@ -52,8 +52,8 @@ NCU_TRAFFIC = {
     # one-pass ncu captures (dram__bytes_read.sum + dram__bytes_write.sum) of one launch at
     # 256^3, the 4th after 3 warm-ups, in the shapes the autotuner picks; summary in
     # profiles/bench_256_launch_list.md.
-    "ec75da79f4957a5e:16x16, balanced": 1420000000 + 642890000,
-    "ec75da79f4957a5e:32x8, balanced": 1560000000 + 644230000,
+    "0eda1e22a9f14107:16x16, balanced, TMA": 1420000000 + 643290000,
+    "0eda1e22a9f14107:32x8, balanced, TMA": 1560000000 + 645140000,
 }
 
 
