@@ -15,8 +15,10 @@
 //    differences become  S2 - 4 S1 + 18 U(p)  with S2 the sum of the six values at
 //    distance 2 and S1 the six at distance 1; combined with the flux sum by one FMA with
 //    the folded constant -eps.
-//  * Every add, subtract and multiply is issued as an FMA (see Pipe in acs_internal.cuh):
-//    on GB300 DFMA issues faster than DADD/DMUL, and the results are bit-identical.
+//  * Every add, subtract and multiply is issued as an FMA whose constant operands sit in
+//    registers (see Pipe in device_ops.cuh): on GB300 an FP64 instruction with three register
+//    operands issues faster than DADD/DMUL or a DFMA with a constant-bank operand, and the
+//    results are bit-identical.
 //  * Bulk load (Sec. VI-B): each xy-plane of U, with a 2-cell halo, is copied into a ring
 //    of five shared-memory slots one step ahead of its use (element-wise with cp.async, or
 //    with ACS_TILE_TMA as one tensor copy per plane completing on an mbarrier), so every load
