@@ -52,16 +52,22 @@ NCU_TRAFFIC = {
     # one-pass ncu captures (dram__bytes_read.sum + dram__bytes_write.sum) of one launch at
     # 256^3, the 4th after 3 warm-ups, in the shapes the autotuner picks; summary in
     # profiles/bench_256_launch_list.md.
-    "0eda1e22a9f14107:16x16, balanced, TMA": 1420000000 + 643290000,
-    "0eda1e22a9f14107:32x8, balanced, TMA": 1560000000 + 645140000,
+    "65a5e038e2cfce15:16x16, balanced, TMA": 1420000000 + 643290000,
+    "65a5e038e2cfce15:32x8, balanced, TMA": 1560000000 + 645140000,
 }
 
 
 def kernel_source_hash() -> str:
+    """Hash of the code (comments and whitespace removed) of the files that define the
+    saturated RHS kernel: a comment edit keeps the recorded ncu traffic, a code edit drops it."""
+    import re
     h = hashlib.sha256()
-    for f in ("march.cuh", "rhs_saturated.cu", "device_ops.cuh"):
-        with open(os.path.join(ROOT, "paper_2306_13002_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    for f in ("march.cuh", "rhs_saturated.cu", "device_ops.cuh", "tma.cuh"):
+        with open(os.path.join(ROOT, "paper_2306_13002_gb300", "csrc", f)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 
