@@ -163,10 +163,11 @@ acs_status acs_rhs_saturated(const double *U, double *R, const acs_grid *g, cons
  *   tile   launch shape of the slab kernels or NULL (16 x 16, balanced schedule, TMA staging).
  *   ws     device workspace of acs_rhs_host_workspace_bytes(g, slab) bytes (three input and
  *          three output slab buffers), 16-byte aligned.
- * Uploads, the slab kernels (alternating between two streams) and downloads run on four
- * library-owned streams per device, ordered by events; the first upload waits for the work
- * already enqueued on `stream`, and on return `stream` is ordered after the last download (so a
- * later cudaStreamSynchronize(stream) means R is complete on the host). Each input plane
+ * Uploads, halo-plane copies, the slab kernels (alternating between two streams) and downloads
+ * run on five library-owned streams per device, ordered by events (concurrent calls on one
+ * device share those streams, so their copies queue behind each other). The first upload
+ * waits for the work already enqueued on `stream`, and on return `stream` is ordered after the
+ * last download (so a later cudaStreamSynchronize(stream) means R is complete on the host). Each input plane
  * crosses the host link once (the halo planes shared by consecutive slabs are copied on the
  * device by a small kernel).
  */
