@@ -73,6 +73,25 @@ int resident_blocks(const void* fn, int threads, size_t smem_bytes) {
     return n;
 }
 
+BalancedPlan balanced_plan(i64 C, int ntx, int Z, int G) {
+    // Warm-up of one segment (prologue loads, one extra plane of own-point fluxes) in plane
+    // steps, the figure default_kchunk uses.
+    const double o = 0.35;
+    BalancedPlan s{ntx, Z, G, (int)(C / G), (int)(C % G), 0};
+    if (s.R == 0) return s;
+    const int T = G - s.R;
+    double best = 1e300;
+    for (int P = 1; P < Z; ++P) {
+        const double top = (double)s.R * (Z - P) / T;
+        const double cost = std::max(P + o, top + o * (top / (Z - P) + 1.0));
+        if (cost < best - 1e-9) {
+            best = cost;
+            s.P = P;
+        }
+    }
+    return s;   // P = 0 (Z == 1): the other G - R blocks take all R columns
+}
+
 static __device__ unsigned int g_wait_timeouts = 0;
 
 unsigned* wait_timeout_counter() {

@@ -105,6 +105,9 @@ unsigned* wait_timeout_counter();
 // origin i0 - r + halo must be a multiple of 2 elements).
 acs_status encode_plane_map(const double* base, const Geom& g, int ncomp, int box_x, int box_y, CUtensorMap* map);
 
+// The balanced schedule of C column tiles (ntx along x) by Z planes on G blocks.
+BalancedPlan balanced_plan(i64 C, int ntx, int Z, int G);
+
 // Blocks of `fn` that fit on the whole device at once (0 if the query fails); cached per
 // kernel and device. ensure_smem must have been called for fn first.
 int resident_blocks(const void* fn, int threads, size_t smem_bytes);

@@ -15,6 +15,48 @@ struct Geom {
     i64 osy, osz, osc;
 };
 
+// Balanced schedule (ACS_TILE_BALANCED) of C column tiles x Z planes over G resident blocks,
+// laid out so that blocks running at the same time work on neighbouring columns at the same z
+// (the halo planes they share are then still in L2):
+//  1. f = C / G whole rounds: in round r block b marches column r G + b over all Z planes;
+//  2. the R = C - f G remaining columns: block b < R marches the base [0, P) of column f G + b,
+//     the other G - R blocks split the tops [P, Z) of those R columns (column by column, z in
+//     order) into equal contiguous shares. The host picks P so that a base and a top share cost
+//     the same, counting each segment's warm-up (balanced_plan).
+struct BalancedPlan {
+    int ntx;   // column tiles along x; column c is tile (c % ntx, c / ntx)
+    int Z;     // planes per column
+    int G;     // blocks launched
+    int f;     // whole rounds
+    int R;     // columns left after the rounds
+    int P;     // base height of the remaining columns
+};
+
+// Calls seg(column, z0, z1) for every segment of block b, in order.
+template <class Seg>
+__device__ __forceinline__ void balanced_segments(const BalancedPlan& s, int b, Seg&& seg) {
+    for (int r = 0; r < s.f; ++r) seg((i64)r * s.G + b, 0, s.Z);
+    if (s.R == 0) return;
+    const i64 c0 = (i64)s.f * s.G;
+    if (b < s.R) {
+        if (s.P > 0) seg(c0 + b, 0, s.P);
+        return;
+    }
+    const int H = s.Z - s.P;   // height of each top
+    const int T = s.G - s.R;
+    const i64 Wt = (i64)s.R * H;
+    const int t = b - s.R;
+    i64 L = Wt * t / T;
+    const i64 L1 = Wt * (t + 1) / T;
+    while (L < L1) {
+        const i64 col = L / H;
+        const int z0 = (int)(L - col * H);
+        const int z1 = (int)min((i64)H, z0 + (L1 - L));
+        seg(c0 + col, s.P + z0, s.P + z1);
+        L += z1 - z0;
+    }
+}
+
 // FP64 instruction selection for the saturated kernels. Measured on GB300: an FP64
 // instruction whose operands are two per-thread registers and nothing else from a register
 // (DADD, DMUL, or a DFMA whose third operand is an immediate or a kernel argument) issues at

@@ -45,32 +45,23 @@ __global__ void __launch_bounds__(BX * BY, RhsShape<BX, BY>::MINB)
                            tmo);
 }
 
-// Balanced schedule (ACS_TILE_BALANCED): one block per resident slot. The work is the list
-// of (column tile, z-plane) pairs, columns in x-fastest order and each column's planes in
-// order; block b marches the contiguous share [W b / G, W (b + 1) / G) of its W pairs (one
-// or two column segments when G exceeds the column count, whole columns plus two partial
-// ones otherwise). Every block gets the same number of planes (to one), so there is no partly
-// filled last wave, and a grid of C columns pays about C + G segment warm-ups instead of one
-// per z-chunk. Neighbouring columns run at different z, so their shared halo planes are read
-// from DRAM again (about 2x the input bytes); a variant that kept all blocks at the same z
-// (whole-column rounds, then base/top shares) read 1.18x the input but ran 0.3-1.4 % slower
-// on GB300, and this kernel is bound by the FP64 pipe, not by DRAM.
+// Balanced schedule (ACS_TILE_BALANCED): one block per resident slot, marching the segments
+// BalancedPlan gives it (whole columns in rounds, then a base or an equal share of the tops of
+// the remaining columns). Every block gets the same work to about one plane step, so there is
+// no partly filled last wave, and a grid of C columns pays about C + G segment warm-ups
+// instead of one per z-chunk. Blocks running together march neighbouring columns at the same
+// z, so the halo planes they share are read from L2: 1.2x the input from DRAM at 256^3,
+// against 2x for the plain contiguous split of the (column, plane) list, which also ran
+// 0.1-1.9 % slower.
 template <int BX, int BY, bool TMA>
 __global__ void __launch_bounds__(BX * BY, RhsShape<BX, BY>::MINB)
     rhs_saturated_balanced_kernel(const double* __restrict__ U, double* __restrict__ R, Geom g, RhsConst k,
-                                  const __grid_constant__ CUtensorMap map, unsigned* tmo) {
+                                  BalancedPlan plan, const __grid_constant__ CUtensorMap map, unsigned* tmo) {
     extern __shared__ __align__(128) double smem[];
-    const int ntx = (g.nx + BX - 1) / BX;
-    const i64 W = (i64)ntx * ((g.ny + BY - 1) / BY) * g.nz;
-    i64 L = W * blockIdx.x / gridDim.x;
-    const i64 L1 = W * (blockIdx.x + 1) / gridDim.x;
-    while (L < L1) {
-        const i64 col = L / g.nz;
-        const int z0 = (int)(L - col * g.nz);
-        const int z1 = (int)min((i64)g.nz, z0 + (L1 - L));
-        rhs_march<BX, BY, TMA>(U, R, g, k, (int)(col % ntx) * BX, (int)(col / ntx) * BY, z0, z1, smem, &map, tmo);
-        L += z1 - z0;
-    }
+    balanced_segments(plan, blockIdx.x, [&](i64 col, int z0, int z1) {
+        rhs_march<BX, BY, TMA>(U, R, g, k, (int)(col % plan.ntx) * BX, (int)(col / plan.ntx) * BY, z0, z1, smem,
+                               &map, tmo);
+    });
 }
 
 template <int BX, int BY, bool TMA>
@@ -83,12 +74,14 @@ acs_status launch_tt(const double* U, double* R, const Geom& g, const RhsConst& 
         const void* fn = (const void*)rhs_saturated_balanced_kernel<BX, BY, TMA>;
         acs_status st = ensure_smem(fn, S::BYTES);
         if (st != ACS_OK) return st;
-        const i64 W = (i64)((g.nx + BX - 1) / BX) * ((g.ny + BY - 1) / BY) * g.nz;
+        const int ntx = (g.nx + BX - 1) / BX;
+        const i64 C = (i64)ntx * ((g.ny + BY - 1) / BY);
         i64 G = resident_blocks(fn, S::NT, S::BYTES);
         if (G <= 0) return fail(ACS_ERR_CUDA, "occupancy query failed for rhs_saturated_balanced_kernel");
-        if (G > W) G = W;
-        rhs_saturated_balanced_kernel<BX, BY, TMA><<<(unsigned)G, dim3(BX, BY, 1), S::BYTES, s>>>(U, R, g, k, map,
-                                                                                                 tmo);
+        if (G > C * g.nz) G = C * g.nz;
+        const BalancedPlan plan = balanced_plan(C, ntx, g.nz, (int)G);
+        rhs_saturated_balanced_kernel<BX, BY, TMA><<<(unsigned)G, dim3(BX, BY, 1), S::BYTES, s>>>(U, R, g, k, plan,
+                                                                                                 map, tmo);
         return launch_status("rhs_saturated_balanced_kernel");
     }
     const void* fn = (const void*)rhs_saturated_kernel<BX, BY, TMA>;

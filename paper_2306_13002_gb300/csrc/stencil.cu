@@ -54,26 +54,18 @@ __global__ void __launch_bounds__(BX * BY, StarShape<BX, BY>::MINB)
                             &map, tmo);
 }
 
-// Balanced schedule (ACS_TILE_BALANCED): one block per resident slot, each marching an equal
-// contiguous share of the (column tile, z-plane) list, as rhs_saturated_balanced_kernel does.
+// Balanced schedule (ACS_TILE_BALANCED): one block per resident slot, marching the segments
+// BalancedPlan gives it, as rhs_saturated_balanced_kernel does.
 template <int BX, int BY, bool TMA>
 __global__ void __launch_bounds__(BX * BY, StarShape<BX, BY>::MINB)
     star_saturated_balanced_kernel(const double* __restrict__ u, const double* __restrict__ a,
-                                   double* __restrict__ out, Geom g, StarCoef cf,
+                                   double* __restrict__ out, Geom g, StarCoef cf, BalancedPlan plan,
                                    const __grid_constant__ CUtensorMap map, unsigned* tmo) {
     extern __shared__ __align__(128) double smem[];
-    const int ntx = (g.nx + BX - 1) / BX;
-    const i64 W = (i64)ntx * ((g.ny + BY - 1) / BY) * g.nz;
-    i64 L = W * blockIdx.x / gridDim.x;
-    const i64 L1 = W * (blockIdx.x + 1) / gridDim.x;
-    while (L < L1) {
-        const i64 col = L / g.nz;
-        const int z0 = (int)(L - col * g.nz);
-        const int z1 = (int)min((i64)g.nz, z0 + (L1 - L));
-        star_march<BX, BY, TMA>(u, a, out, g, cf, (int)(col % ntx) * BX, (int)(col / ntx) * BY, z0, z1, smem, &map,
-                                tmo);
-        L += z1 - z0;
-    }
+    balanced_segments(plan, blockIdx.x, [&](i64 col, int z0, int z1) {
+        star_march<BX, BY, TMA>(u, a, out, g, cf, (int)(col % plan.ntx) * BX, (int)(col / plan.ntx) * BY, z0, z1,
+                                smem, &map, tmo);
+    });
 }
 
 template <int BX, int BY, bool TMA>
@@ -86,12 +78,14 @@ acs_status launch_star_tt(const double* u, const double* a, double* out, const G
         const void* fb = (const void*)star_saturated_balanced_kernel<BX, BY, TMA>;
         acs_status st = ensure_smem(fb, S::BYTES);
         if (st != ACS_OK) return st;
-        const i64 W = (i64)((g.nx + BX - 1) / BX) * ((g.ny + BY - 1) / BY) * g.nz;
+        const int ntx = (g.nx + BX - 1) / BX;
+        const i64 C = (i64)ntx * ((g.ny + BY - 1) / BY);
         i64 G = resident_blocks(fb, S::NT, S::BYTES);
         if (G <= 0) return fail(ACS_ERR_CUDA, "occupancy query failed for star_saturated_balanced_kernel");
-        if (G > W) G = W;
+        if (G > C * g.nz) G = C * g.nz;
+        const BalancedPlan plan = balanced_plan(C, ntx, g.nz, (int)G);
         star_saturated_balanced_kernel<BX, BY, TMA><<<(unsigned)G, dim3(BX, BY, 1), S::BYTES, s>>>(u, a, out, g, c,
-                                                                                                   map, tmo);
+                                                                                                   plan, map, tmo);
         return launch_status("star_saturated_balanced_kernel");
     }
     const void* fn = (const void*)star_saturated_kernel<BX, BY, TMA>;
