@@ -52,8 +52,8 @@ NCU_TRAFFIC = {
     # one-pass ncu captures (dram__bytes_read.sum + dram__bytes_write.sum) of one launch at
     # 256^3, the 4th after 3 warm-ups, in the shapes the autotuner picks; summary in
     # profiles/bench_256_launch_list.md.
-    "65a5e038e2cfce15:16x16, balanced, TMA": 1420000000 + 643290000,
-    "65a5e038e2cfce15:32x8, balanced, TMA": 1560000000 + 645140000,
+    "d165b6d2a2dc2d20:16x16, balanced, TMA": 833190000 + 634500000,
+    "d165b6d2a2dc2d20:32x8, balanced, TMA": 859060000 + 634710000,
 }
 
 
