@@ -76,6 +76,33 @@ def test_rhs_balanced_whole_rounds(dims, tile):
     assert_parity(R, ref, what=f"rhs balanced {dims} tile {tile}")
 
 
+@pytest.mark.parametrize("dims,tile", [((320, 320, 1), (16, 16, 0, 3)), ((320, 304, 2), (16, 16, 0, 1)),
+                                       ((40, 40, 300), (16, 16, 0, 3))])
+def test_rhs_balanced_plan_edges(dims, tile):
+    """The balanced plan's edge cases: one plane (no base, the remaining columns split among the
+    other blocks), two planes, and a tall grid with few columns (more blocks than columns)."""
+    nx, ny, nz = dims
+    U = inputs.rhs_field(nx, ny, nz, halo=2, seed=1600 + nz)
+    ref = oracle.rhs(U, threads=4)
+    assert_parity(_rhs_gpu("saturated", U, tile=tile).cpu().numpy(), ref, what=f"rhs balanced {dims} {tile}")
+
+
+@pytest.mark.parametrize("kind", ["rhs", "star"])
+def test_tma_and_elementwise_staging_agree_bitwise(kind):
+    """The two plane stagings move the same values into the same ring, so the results are
+    bit-identical (z-chunked and balanced launches)."""
+    if kind == "rhs":
+        U = inputs.rhs_field(70, 46, 33, halo=2, seed=1700)
+        runs = [_rhs_gpu("saturated", U, tile=t).cpu().numpy() for t in
+                ((16, 16, 5, 0), (16, 16, 5, 2), (32, 8, 0, 1), (32, 8, 0, 3))]
+    else:
+        u, a = inputs.stencil_fields(70, 46, 33, halo=4, seed=1701)
+        runs = [_star_gpu("saturated", u, a, tile=t).cpu().numpy() for t in
+                ((32, 8, 5, 0), (32, 8, 5, 2), (16, 16, 0, 1), (16, 16, 0, 3))]
+    assert np.array_equal(runs[0], runs[1]) and np.array_equal(runs[2], runs[3])
+    assert np.array_equal(runs[0], runs[2])
+
+
 @pytest.mark.parametrize("dims", [(1, 1, 1), (37, 29, 23), (70, 21, 40)])
 def test_rhs_plain_ragged(dims):
     nx, ny, nz = dims
