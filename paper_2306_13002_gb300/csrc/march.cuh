@@ -307,10 +307,17 @@ __device__ __forceinline__ void star_march(const double* __restrict__ u, const d
     // The ring's base rounded up to 128 bytes (a TMA destination must be). This also measured
     // faster for the element-wise staging than addressing the declared base directly.
     double* smem = align128(smem_raw);
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    // A tile cut by the grid's x edge (w < BX valid columns) packs its w x h points into the
+    // first threads, row by row, so that the warps past them carry no point: the FP64 pipe runs
+    // a whole warp if any of its lanes is active. (Points are independent here; the RHS march
+    // cannot do this, its edge threads compute the fluxes of halo points.)
+    const int w = min(BX, g.nx - i0), h = min(BY, g.ny - j0);
+    const int tx = (w == BX) ? (int)threadIdx.x : tid % w;
+    const int ty = (w == BX) ? (int)threadIdx.y : tid / w;
+    const bool active = ty < h;
     const int i = i0 + tx, j = j0 + ty;
-    const bool active = (i < g.nx) && (j < g.ny);
-    const int own = (ty + 4) * PX + (tx + 4);
+    const int own = active ? (ty + 4) * PX + (tx + 4) : 4 * PX + 4;   // inactive: any cell of the slot
     auto sidx = [&](int q) -> int { return (q + S::NSLOT) % S::NSLOT; };
     auto slot = [&](int q) -> double* { return smem + sidx(q) * PLANE; };
 
