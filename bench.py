@@ -52,8 +52,8 @@ NCU_TRAFFIC = {
     # one-pass ncu captures (dram__bytes_read.sum + dram__bytes_write.sum) of one launch at
     # 256^3, the 4th after 3 warm-ups, in the shapes the autotuner picks; summary in
     # profiles/bench_256_launch_list.md.
-    "d165b6d2a2dc2d20:16x16, balanced, TMA": 833190000 + 634500000,
-    "d165b6d2a2dc2d20:32x8, balanced, TMA": 859060000 + 634710000,
+    "c776320050a5a751:16x16, balanced, TMA": 833130000 + 634700000,
+    "c776320050a5a751:32x8, balanced, TMA": 861060000 + 635180000,
 }
 
 
