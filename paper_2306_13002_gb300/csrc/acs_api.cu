@@ -659,6 +659,6 @@ acs_status acs_wait_timeouts(unsigned int* count) {
     return ACS_OK;
 }
 
-int acs_abi_version(void) { return 100; }
+int acs_abi_version(void) { return 101; }
 
 }  // extern "C"
