@@ -380,7 +380,7 @@ acs_status acs_wait_timeouts(unsigned int *count);
 const char *acs_last_error(void);
 
 /* ABI version of this library (major * 100 + minor): 101 adds ACS_TILE_BALANCED,
- * ACS_TILE_TMA and acs_wait_timeouts to 100; calls valid under 100 behave the same. */
+ * ACS_TILE_TMA and acs_wait_timeouts to 100; calls valid under 100 give the same results. */
 int acs_abi_version(void);
 
 #ifdef __cplusplus
