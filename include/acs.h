@@ -63,7 +63,7 @@ typedef enum acs_status {
     ACS_ERR_INVALID = 1,     /* null pointer, bad size, stride or parameter */
     ACS_ERR_ALIGN = 2,       /* a pointer or stride breaks an alignment the kernel needs */
     ACS_ERR_CUDA = 3,        /* a CUDA runtime call or a kernel launch failed */
-    ACS_ERR_UNSUPPORTED = 4, /* valid request that this build does not implement */
+    ACS_ERR_UNSUPPORTED = 4, /* valid request that the library does not implement */
     ACS_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
     ACS_ERR_NOMODEL = 6,     /* no ranker model was supplied where one is required */
     ACS_ERR_ALIAS = 7,       /* an output overlaps an input */
