@@ -111,6 +111,28 @@ def test_rhs_plain_ragged(dims):
     assert_parity(_rhs_gpu("plain", U).cpu().numpy(), ref, what=f"rhs plain {dims}")
 
 
+@pytest.mark.parametrize("tile", [(16, 16, 0, 3), (32, 8, 4, 2)])
+def test_rhs_tma_staging_with_padded_rows(tile):
+    """TMA staging on a non-compact input (row pitch 48 for rows of 41, planes of that pitch)
+    and an output written into the interior of a larger buffer: the tensor map takes the
+    strides, and nothing outside the interior is written."""
+    nx, ny, nz = 37, 21, 19
+    U = inputs.rhs_field(nx, ny, nz, halo=2, seed=3002)
+    h, gamma, eps = (0.5, 1.0, 1.5), 1.3, 0.3
+    ref = oracle.rhs(U, gamma=gamma, eps=eps, h=h)
+    Ud = padded_dev(U, 48)   # even pitch: TMA needs row and plane strides of whole 16-byte units
+    assert Ud.stride(-2) == 48 and Ud.stride(-3) % 2 == 0
+    big = torch.full((5, nz + 2, ny + 3, nx + 6), float("nan"), dtype=torch.float64, device="cuda")
+    Rd = big[:, 1:1 + nz, 2:2 + ny, 3:3 + nx]
+    before = binding.acs_wait_timeouts()
+    _rhs_gpu("saturated", U, h=h, gamma=gamma, eps=eps, tile=tile, U_dev=Ud, R_dev=Rd)
+    assert_parity(Rd.cpu().numpy(), ref, what=f"rhs tma padded {tile}")
+    mask = torch.ones_like(big, dtype=torch.bool)
+    mask[:, 1:1 + nz, 2:2 + ny, 3:3 + nx] = False
+    assert torch.isnan(big[mask]).all(), "wrote outside the interior"
+    assert binding.acs_wait_timeouts() == before
+
+
 @pytest.mark.parametrize("form", ["plain", "saturated"])
 def test_rhs_parameters_halo_and_strides(form):
     """Non-unit spacing per axis, other gamma/eps, a halo of 3, padded input rows and an
