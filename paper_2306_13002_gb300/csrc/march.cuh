@@ -100,10 +100,20 @@ __device__ __forceinline__ void rhs_march(const double* __restrict__ U, double* 
     uint64_t* bars = reinterpret_cast<uint64_t*>(Cs + S::CONST_ELEMS);
     static_assert(sizeof(RhsRegs) <= S::CONST_ELEMS * sizeof(double), "constant staging area");
 
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    // A tile cut by the grid's x edge (w < BX valid columns) packs its flux points, the w valid
+    // columns and the halo column after them (whose F_x the last valid column differences),
+    // into the first threads row by row; the warps past them compute nothing (the FP64 pipe
+    // runs a whole warp if any lane is active). Rows are not packed: every row up to BY - 1
+    // and the ring row BY are computed as before.
+    const int w = min(BX, g.nx - i0);
+    const int wf = w < BX ? w + 1 : BX;
+    const int tx = w < BX ? tid % wf : (int)threadIdx.x;
+    const int ty = w < BX ? tid / wf : (int)threadIdx.y;
+    const bool fluxer = ty < BY;
     const int i = i0 + tx, j = j0 + ty;
-    const bool active = (i < g.nx) && (j < g.ny);
-    const int own = (ty + 2) * PX + (tx + 2);
+    const bool active = fluxer && tx < w && j < g.ny;
+    const int own = fluxer ? (ty + 2) * PX + (tx + 2) : 2 * PX + 2;   // non-fluxers: any cell
     auto sidx = [&](int q) -> int { return (q + S::NSLOT) % S::NSLOT; };
     auto slot = [&](int q) -> double* { return Us + sidx(q) * (5 * PLANE); };
     auto parity = [&](int q) -> unsigned { return (unsigned)((q - k0 + 2) / S::NSLOT) & 1u; };
@@ -147,8 +157,9 @@ __device__ __forceinline__ void rhs_march(const double* __restrict__ U, double* 
     const RhsRegs kr = stage_consts_read<RhsRegs>(Cs);
     const RhsConst& k = kr.k;
 
-    double fzm[4], fz0[4], fzp[4], pfx[4], pfy[4];
-    {
+    double fzm[4] = {0, 0, 0, 0}, fz0[4] = {0, 0, 0, 0}, fzp[4] = {0, 0, 0, 0};
+    double pfx[4] = {0, 0, 0, 0}, pfy[4] = {0, 0, 0, 0};
+    if (fluxer) {
         const double* s = slot(k0 - 1);
         double ux[4], uy[4];
         point_flux(s[own], s[PLANE + own], s[2 * PLANE + own], s[3 * PLANE + own], s[4 * PLANE + own], k, ux, uy, fzm);
@@ -159,10 +170,12 @@ __device__ __forceinline__ void rhs_march(const double* __restrict__ U, double* 
     for (int kk = k0; kk < k1; ++kk) {
         const double* s0 = slot(kk);
         // (1) x/y fluxes of plane kk: own point (computed one step earlier) and the ring.
+        if (fluxer) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            Fxs[(c * BY + ty) * (BX + 2) + tx + 1] = pfx[c];
-            Fys[(c * (BY + 2) + ty + 1) * BX + tx] = pfy[c];
+            for (int c = 0; c < 4; ++c) {
+                Fxs[(c * BY + ty) * (BX + 2) + tx + 1] = pfx[c];
+                Fys[(c * (BY + 2) + ty + 1) * BX + tx] = pfy[c];
+            }
         }
         // The y-ring (rows -1 and BY) takes threads [0, 2 BX) and the x-ring (columns -1 and
         // BX) the next 2 BY; 2 BX is a multiple of 32, so each warp computes one kind and
@@ -184,7 +197,7 @@ __device__ __forceinline__ void rhs_march(const double* __restrict__ U, double* 
             for (int c = 0; c < 4; ++c) Fxs[(c * BY + ry) * (BX + 2) + rx + 1] = fx[c];
         }
         // (2) all fluxes of the own point at plane kk+1.
-        {
+        if (fluxer) {
             const double* s = slot(kk + 1);
             point_flux(s[own], s[PLANE + own], s[2 * PLANE + own], s[3 * PLANE + own], s[4 * PLANE + own], k, pfx, pfy,
                        fzp);
