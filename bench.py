@@ -52,8 +52,8 @@ NCU_TRAFFIC = {
     # one-pass ncu captures (dram__bytes_read.sum + dram__bytes_write.sum) of one launch at
     # 256^3, the 4th after 3 warm-ups, in the shapes the autotuner picks; summary in
     # profiles/bench_256_launch_list.md.
-    "c776320050a5a751:16x16, balanced, TMA": 833130000 + 634700000,
-    "c776320050a5a751:32x8, balanced, TMA": 861060000 + 635180000,
+    "f5e3d32491a900e9:16x16, balanced, TMA": 831502592 + 633517312,
+    "f5e3d32491a900e9:32x8, balanced, TMA": 857585664 + 633793024,
 }
 
 

@@ -64,6 +64,20 @@ def test_rhs_saturated_ragged(dims, tile):
     assert_parity(R, ref, what=f"rhs saturated {dims} tile {tile}")
 
 
+@pytest.mark.parametrize("tile", [(16, 16, 0, 3), (32, 8, 0, 3), (64, 4, 2, 0), (32, 4, 0, 1)])
+@pytest.mark.parametrize("w", ["one", "half", "all_but_one"])
+def test_rhs_saturated_x_edge_tile_widths(tile, w):
+    """An x-edge tile with 1, BX/2 + 1 and BX - 1 valid columns: its flux points (valid columns
+    plus one halo column) are packed into the first threads, wrapping rows at w + 1."""
+    bx, by = tile[0], tile[1]
+    nx = 2 * bx + {"one": 1, "half": bx // 2 + 1, "all_but_one": bx - 1}[w]
+    ny, nz = by + 3, 6
+    U = inputs.rhs_field(nx, ny, nz, halo=2, seed=1400 + nx + ny)
+    ref = oracle.rhs(U, threads=4)
+    R = _rhs_gpu("saturated", U, tile=tile).cpu().numpy()
+    assert_parity(R, ref, what=f"rhs saturated x-edge {nx}x{ny}x{nz} tile {tile}")
+
+
 @pytest.mark.parametrize("dims,tile", [((288, 288, 5), (16, 16, 0, 1)), ((288, 290, 4), (32, 8, 0, 1)),
                                        ((288, 288, 5), (16, 16, 0, 3))])
 def test_rhs_balanced_whole_rounds(dims, tile):
