@@ -209,7 +209,8 @@ acs_status acs_stencil_saturated(const double *u, const double *a, double *out, 
  *
  * Each grid is cut into work units (tile x z-chunk); a persistent grid of blocks pops units
  * from an atomic counter kept in a caller-provided device workspace, so any number of
- * grids costs one launch. Use: acs_batch_workspace_bytes(n) -> allocate -> acs_batch_prepare
+ * grids costs one launch. Grids run largest first; the smallest ones, whose units make up
+ * about the last two waves of blocks, use z-chunks a quarter of tile->kchunk long. Use: acs_batch_workspace_bytes(n) -> allocate -> acs_batch_prepare
  * (validates every item, uploads the unit table, synchronises `stream`) -> acs_batch_launch
  * as often as needed. acs_batch_launch enqueues a memset of the counter and one kernel on
  * `stream`; it may be captured in a CUDA graph. The items' buffers and the workspace must

@@ -5,7 +5,8 @@
 // an atomic counter in the caller's workspace and runs the same tile march as the
 // single-grid saturated kernels (march.cuh), so the batch needs one launch however many
 // grids it holds. Grids are ordered largest first, so the long units start early and the
-// small ones fill the tail (longest-processing-time order).
+// small ones fill the tail (longest-processing-time order); the last grids in that order
+// take shorter z-chunks (guided self-scheduling), so the blocks run dry closer together.
 //
 // Workspace layout (device memory owned by the caller, 16-byte aligned):
 //   [0, 64)                BatchHeader (the work counter, the unit total, the shape)
@@ -28,7 +29,7 @@ struct BatchDesc {
     const double* in1;  // unused (RHS) or a (stencil)
     double* out;
     Geom g;
-    int ntx, nty, nkc, pad;
+    int ntx, nty, nkc, kchunk;   // this grid's z-chunk (see batch_pack)
 };
 
 struct BatchHeader {
@@ -67,7 +68,6 @@ __global__ void __launch_bounds__(BX * BY, KIND == ACS_KIND_RHS ? RhsShape<BX, B
     const int n = h->n;
     const long long* prefix = reinterpret_cast<const long long*>(ws + kHeader + desc_bytes(n));
     const long long total = h->total;
-    const int kchunk = h->kchunk;
     const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
     for (;;) {
         if (leader) s_unit = (long long)atomicAdd(counter, 1ULL);
@@ -82,8 +82,8 @@ __global__ void __launch_bounds__(BX * BY, KIND == ACS_KIND_RHS ? RhsShape<BX, B
         lu /= d.ntx;
         const int ty = (int)(lu % d.nty);
         const int kc = (int)(lu / d.nty);
-        const int k0 = kc * kchunk;
-        const int k1 = min(k0 + kchunk, d.g.nz);
+        const int k0 = kc * d.kchunk;
+        const int k1 = min(k0 + d.kchunk, d.g.nz);
         if (KIND == ACS_KIND_RHS)
             rhs_march<BX, BY, false>(d.in0, d.out, d.g, rk, tx * BX, ty * BY, k0, k1, smem, nullptr, nullptr);
         else
@@ -139,15 +139,28 @@ acs_status batch_pack(const acs_batch_item* items, const Geom* geo, int n, int k
                       std::vector<unsigned char>& image, long long& total) {
     std::vector<int> order(n);
     std::iota(order.begin(), order.end(), 0);
-    std::vector<long long> units(n);
-    for (int q = 0; q < n; ++q) {
-        const Geom& g = geo[q];
-        const long long ntx = (g.nx + tile.bx - 1) / tile.bx, nty = (g.ny + tile.by - 1) / tile.by;
-        const long long nkc = (g.nz + tile.kchunk - 1) / tile.kchunk;
-        units[q] = ntx * nty * nkc;
-    }
     auto points = [&](int q) { return (long long)geo[q].nx * geo[q].ny * geo[q].nz; };
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return points(x) > points(y); });
+    // Guided z-chunks: the grids at the end of the order, whose units make up the last two
+    // waves of the queue (two units per resident block, estimated), take z-chunks a quarter
+    // as long, so the blocks run out of work closer together.
+    const long long waves = 2LL * num_sms() * (kind == ACS_KIND_RHS ? 2 : 4);
+    const int tail_kchunk = std::max(1, tile.kchunk / 4);
+    std::vector<int> kchunk(n, tile.kchunk);
+    std::vector<long long> units(n);
+    auto unit_count = [&](int q, int kc) {
+        const Geom& g = geo[q];
+        const long long ntx = (g.nx + tile.bx - 1) / tile.bx, nty = (g.ny + tile.by - 1) / tile.by;
+        return ntx * nty * ((g.nz + kc - 1) / kc);
+    };
+    long long tail = 0;
+    for (int r = n - 1; r >= 0; --r) {
+        const int q = order[r];
+        tail += unit_count(q, tail_kchunk);
+        if (tail > waves) break;
+        kchunk[q] = tail_kchunk;
+    }
+    for (int q = 0; q < n; ++q) units[q] = unit_count(q, kchunk[q]);
     image.assign(batch_ws_bytes(n), 0);
     BatchHeader h;
     std::memset(&h, 0, sizeof(h));
@@ -170,7 +183,8 @@ acs_status batch_pack(const acs_batch_item* items, const Geom* geo, int n, int k
         e.g = g;
         e.ntx = (g.nx + tile.bx - 1) / tile.bx;
         e.nty = (g.ny + tile.by - 1) / tile.by;
-        e.nkc = (g.nz + tile.kchunk - 1) / tile.kchunk;
+        e.nkc = (g.nz + kchunk[q] - 1) / kchunk[q];
+        e.kchunk = kchunk[q];
         d[r] = e;
         prefix[r] = acc;
         acc += units[q];
