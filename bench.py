@@ -381,6 +381,8 @@ def main() -> None:
     ap.add_argument("--tile", default="", help="bx,by,kchunk[,flags]: use this launch shape instead of the autotuner")
     ap.add_argument("--large", action="store_true",
                     help="instead of the step benchmark: RHS 512^3 and star stencil 768^3, all forms")
+    ap.add_argument("--batch", action="store_true",
+                    help="instead of the step benchmark: the 64-grid star-stencil batch alone")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     args.steps = max(args.steps, 1)
@@ -389,6 +391,15 @@ def main() -> None:
         return
     if args.large:
         run_large(args)
+        return
+    if args.batch:
+        import torch
+        from paper_2306_13002_gb300 import binding, inputs
+        from paper_2306_13002_gb300 import build as acs_build
+        acs_build.build()
+        stream = torch.cuda.current_stream()
+        res = bench_batch(torch, binding, inputs, stream, max(3, min(args.steps, 50)))
+        print(json.dumps({"workload": "star_stencil_batch_64_grids_fp64", "unit": "ms per batch", **res}))
         return
     if args.ranker:
         from paper_2306_13002_gb300 import build as acs_build

@@ -68,6 +68,47 @@ def test_rhs_batch_matches_oracle(tile):
         assert_parity(R.cpu().numpy(), oracle.rhs(U, h=(1.0, 0.5, 2.0)), what=f"rhs batch {U.shape}")
 
 
+def _guided_units(sides, bx, by, kchunk, per_sm):
+    """Unit count of a batch plan: grids largest first; the last grids whose units (in chunks
+    of kchunk // 4) fit in two waves of resident blocks take the short chunks."""
+    waves = 2 * torch.cuda.get_device_properties(0).multi_processor_count * per_sm
+    order = sorted(range(len(sides)), key=lambda q: -int(np.prod(sides[q])))   # stable, largest first
+    tail_kc = max(1, kchunk // 4)
+
+    def units(q, kc):
+        nx, ny, nz = (int(v) for v in sides[q])
+        return -(-nx // bx) * -(-ny // by) * -(-nz // kc)
+
+    kcs = {q: kchunk for q in order}
+    acc = 0
+    for q in reversed(order):
+        acc += units(q, tail_kc)
+        if acc > waves:
+            break
+        kcs[q] = tail_kc
+    return sum(units(q, kcs[q]) for q in order)
+
+
+def test_rhs_batch_guided_chunks_head_and_tail():
+    """Twelve 64^3 grids (units of 16 planes, the queue's head) and twenty small grids (the
+    tail, units of 4 planes): parity with the oracle and the plan's unit count."""
+    sides = [(64, 64, 64)] * 12 + [(int(a), int(b), int(c)) for a, b, c in
+                                   inputs.batch_sides(20, seed=inputs.SEED_BATCH + 20, lo=8, hi=40)]
+    grids, host = [], []
+    for q, (nx, ny, nz) in enumerate(sides):
+        U = inputs.rhs_field(nx, ny, nz, halo=2, seed=7700 + q)
+        grids.append((to_dev(U), None, torch.full((5, nz, ny, nx), float("nan"), dtype=torch.float64,
+                                                  device="cuda")))
+        host.append(U)
+    plan = binding.acs_batch_prepare(binding.KIND_RHS, grids, _ws(len(grids)), tile=(16, 16, 16))
+    assert plan.total_units == _guided_units(sides, 16, 16, 16, per_sm=2)
+    assert plan.total_units > 12 * 16 * 4            # some grids keep 16-plane units
+    binding.acs_batch_launch(plan)
+    torch.cuda.synchronize()
+    for U, (_, _, R) in zip(host, grids):
+        assert_parity(R.cpu().numpy(), oracle.rhs(U, threads=8), what=f"rhs guided batch {U.shape}")
+
+
 def test_batch_in_cuda_graph_replays():
     """Capture acs_batch_launch once; replay after changing the inputs in place."""
     sides = inputs.batch_sides(12, seed=inputs.SEED_BATCH + 1)
