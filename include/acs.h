@@ -377,11 +377,23 @@ const char *acs_status_string(acs_status s);
  */
 acs_status acs_wait_timeouts(unsigned int *count);
 
+/*
+ * acs_wait_selftest - run the bounded-wait path once on the current device: one block of 32
+ * threads, each waiting with the saturated kernels' own bounded wait (about one second of
+ * SM clock cycles) on an mbarrier phase that nothing completes, so every wait runs out. Writes
+ * the number of waits that ran out to *timeouts (32 when the path works) and leaves the
+ * acs_wait_timeouts counter alone. No copy is issued, so nothing is left in flight. Enqueued on
+ * `stream`, which it synchronises (takes about one second). ACS_ERR_INVALID for a NULL
+ * timeouts, ACS_ERR_CUDA if the launch or the read fails.
+ */
+acs_status acs_wait_selftest(unsigned int *timeouts, acs_stream stream);
+
 /* Reason for the calling thread's most recent failed call ("" if none). */
 const char *acs_last_error(void);
 
 /* ABI version of this library (major * 100 + minor): 101 adds ACS_TILE_BALANCED,
- * ACS_TILE_TMA and acs_wait_timeouts to 100; calls valid under 100 give the same results. */
+ * ACS_TILE_TMA and acs_wait_timeouts to 100, 102 adds acs_wait_selftest; calls valid under
+ * 100 give the same results. */
 int acs_abi_version(void);
 
 #ifdef __cplusplus

@@ -82,7 +82,7 @@ EXPORTS = ("acs_rhs_plain", "acs_rhs_saturated", "acs_rhs_form", "acs_stencil_pl
            "acs_variant_build", "acs_variant_launch", "acs_variant_free", "acs_ranker_param_count",
            "acs_ranker_workspace_bytes", "acs_ranker_train", "acs_variant_rank", "acs_status_string",
            "acs_last_error", "acs_abi_version", "acs_block_form", "acs_rhs_host_workspace_bytes",
-           "acs_rhs_saturated_host", "acs_wait_timeouts")
+           "acs_rhs_saturated_host", "acs_wait_timeouts", "acs_wait_selftest")
 
 
 def lib() -> ctypes.CDLL:
@@ -156,6 +156,8 @@ def lib() -> ctypes.CDLL:
             L.acs_abi_version.restype = ctypes.c_int
             L.acs_wait_timeouts.argtypes = [ctypes.POINTER(ctypes.c_uint)]
             L.acs_wait_timeouts.restype = st
+            L.acs_wait_selftest.argtypes = [ctypes.POINTER(ctypes.c_uint), ctypes.c_void_p]
+            L.acs_wait_selftest.restype = st
             _lib = L
     return _lib
 
@@ -268,6 +270,14 @@ def acs_wait_timeouts() -> int:
     synchronous, call it after the work has completed."""
     n = ctypes.c_uint(0)
     _check(lib().acs_wait_timeouts(ctypes.byref(n)), "acs_wait_timeouts")
+    return int(n.value)
+
+
+def acs_wait_selftest(stream=None) -> int:
+    """Run the bounded-wait path once (32 waits on an mbarrier phase nothing completes, about
+    one second); returns how many waits ran out (32 when the path works)."""
+    n = ctypes.c_uint(0)
+    _check(lib().acs_wait_selftest(ctypes.byref(n), _stream_ptr(stream)), "acs_wait_selftest")
     return int(n.value)
 
 

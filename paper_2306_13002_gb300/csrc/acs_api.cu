@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "acs_internal.cuh"
+#include "tma.cuh"
 
 namespace acs {
 
@@ -110,6 +111,32 @@ unsigned* wait_timeout_counter() {
     }
     return addr[dev];
 }
+
+namespace {
+
+__device__ unsigned int g_selftest_timeouts = 0;
+
+// One block: every thread waits, with the kernels' bounded wait, on phase 0 of an mbarrier that
+// expects one arrival and never gets it, so each wait runs out after its bound and is counted in
+// shared memory; thread 0 then retires the barrier and publishes the count.
+__global__ void wait_selftest_kernel() {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ unsigned count;
+    if (threadIdx.x == 0) {
+        count = 0;
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    mbar_wait_bounded(&bar, 0u, &count);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_inval(&bar);
+        g_selftest_timeouts = count;
+    }
+}
+
+}  // namespace
 
 acs_status encode_plane_map(const double* base, const Geom& g, int ncomp, int box_x, int box_y, CUtensorMap* map) {
     if ((uintptr_t)base % 16 != 0) return fail(ACS_ERR_ALIGN, "TMA staging needs a 16-byte aligned input");
@@ -659,6 +686,20 @@ acs_status acs_wait_timeouts(unsigned int* count) {
     return ACS_OK;
 }
 
-int acs_abi_version(void) { return 101; }
+acs_status acs_wait_selftest(unsigned int* timeouts, acs_stream stream) {
+    if (!timeouts) return fail(ACS_ERR_INVALID, "timeouts is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    wait_selftest_kernel<<<1, 32, 0, s>>>();
+    acs_status st = launch_status("wait_selftest_kernel");
+    if (st != ACS_OK) return st;
+    unsigned h = 0;
+    if (cudaMemcpyFromSymbolAsync(&h, g_selftest_timeouts, sizeof(h), 0, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return launch_status("cudaMemcpyFromSymbolAsync");
+    if (cudaStreamSynchronize(s) != cudaSuccess) return launch_status("cudaStreamSynchronize");
+    *timeouts = h;
+    return ACS_OK;
+}
+
+int acs_abi_version(void) { return 102; }
 
 }  // extern "C"

@@ -35,7 +35,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_status_strings(lib):
-    assert binding.acs_abi_version() >= 100
+    assert binding.acs_abi_version() >= 102
     for s in range(9):
         assert binding.acs_status_string(s) and binding.acs_status_string(s) != "unknown status"
     assert binding.acs_status_string(99) == "unknown status"
@@ -148,3 +148,7 @@ def test_tune_cache_file_errors(lib, tmp_path):
     assert lib.acs_tune_cache_load(str(p).encode()) == 1
     lib.acs_tune_cache_clear()
     assert lib.acs_tune_cache_size() == 0
+
+
+def test_wait_selftest_rejects_null_output(lib):
+    assert lib.acs_wait_selftest(None, None) == 1        # ACS_ERR_INVALID before any launch
