@@ -324,7 +324,7 @@ __device__ __forceinline__ void star_march(const double* __restrict__ u, const d
     // A tile cut by the grid's x edge (w < BX valid columns) packs its w x h points into the
     // first threads, row by row, so that the warps past them carry no point: the FP64 pipe runs
     // a whole warp if any of its lanes is active. (Points are independent here; the RHS march
-    // cannot do this, its edge threads compute the fluxes of halo points.)
+    // packs its flux points instead, one halo column more than its valid columns.)
     const int w = min(BX, g.nx - i0), h = min(BY, g.ny - j0);
     const int tx = (w == BX) ? (int)threadIdx.x : tid % w;
     const int ty = (w == BX) ? (int)threadIdx.y : tid / w;
