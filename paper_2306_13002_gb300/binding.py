@@ -56,7 +56,7 @@ class BatchPlan(ctypes.Structure):
 
 KIND_RHS, KIND_STENCIL = 0, 1
 TILE_BALANCED = 1  # acs_tile.flags: one block per resident slot, equal (column, plane) shares
-TILE_TMA = 2       # acs_tile.flags: planes staged by TMA tensor copies (star stencil)
+TILE_TMA = 2       # acs_tile.flags: planes staged by TMA tensor copies (single-grid saturated kernels)
 VARIANT_NFEAT = 16
 
 

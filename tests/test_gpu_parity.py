@@ -392,7 +392,8 @@ def test_block_forms_halo2_padded(form):
 
 # ----------------------------------------------------------- streamed host-buffer RHS
 
-@pytest.mark.parametrize("dims,slab", [((37, 29, 71), 16), ((20, 9, 5), 32), ((33, 17, 64), 32), ((8, 8, 1), 0)])
+@pytest.mark.parametrize("dims,slab", [((37, 29, 71), 16), ((20, 9, 5), 32), ((33, 17, 64), 32), ((8, 8, 1), 0),
+                                       ((19, 7, 21), 1), ((19, 7, 23), 3), ((24, 10, 41), 16), ((24, 10, 40), 16)])
 def test_rhs_saturated_host_streamed(dims, slab):
     nx, ny, nz = dims
     U = inputs.rhs_field(nx, ny, nz, halo=2, seed=6500 + nz)
@@ -410,6 +411,21 @@ def test_rhs_saturated_host_streamed(dims, slab):
     binding.acs_rhs_saturated_host(Uh, R2, ws, h=(1.0, 0.5, 2.0), slab=slab, stream=s)
     s.synchronize()
     assert torch.equal(R2, Rh)
+
+
+def test_rhs_saturated_host_pageable_buffers():
+    """Host arrays that are not page-locked: the copies no longer overlap, the results stay the same."""
+    nx, ny, nz = 30, 18, 45
+    U = inputs.rhs_field(nx, ny, nz, halo=2, seed=6600)
+    ref = oracle.rhs(U)
+    Uh = torch.from_numpy(U)
+    Rh = torch.full((5, nz, ny, nx), float("nan"), dtype=torch.float64)
+    ws = torch.empty(binding.acs_rhs_host_workspace_bytes(Uh, Rh, slab=8) // 8 + 2, dtype=torch.float64,
+                     device="cuda")
+    s = torch.cuda.current_stream()
+    binding.acs_rhs_saturated_host(Uh, Rh, ws, slab=8, stream=s)
+    s.synchronize()
+    assert_parity(Rh.numpy(), ref, what="host streamed, pageable")
 
 
 def test_rhs_saturated_host_256_matches_device_path():
