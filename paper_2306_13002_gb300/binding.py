@@ -188,8 +188,21 @@ def _tile(tile) -> ctypes.POINTER(Tile) | None:
     return ctypes.byref(Tile(int(bx), int(by), int(kchunk), int(flags)))
 
 
-def grid_for(inp, out, halo: int, ncomp: int) -> Grid:
-    """acs_grid from an input (halo-extended) and an output tensor's shapes and strides."""
+def _on_device(*tensors) -> None:
+    """The device entry points take device memory: refuse host tensors before any launch."""
+    for t in tensors:
+        if t is not None and not t.is_cuda:
+            raise ValueError("device entry points take CUDA tensors; got a tensor on " + str(t.device))
+
+
+def grid_for(inp, out, halo: int, ncomp: int, host: bool = False) -> Grid:
+    """acs_grid from an input (halo-extended) and an output tensor's shapes and strides; both on
+    the GPU, or both on the host for the host-streamed entry point (host=True)."""
+    if host:
+        if inp.is_cuda or out.is_cuda:
+            raise ValueError("the host-streamed entry point takes host (CPU) tensors")
+    else:
+        _on_device(inp, out)
     if ncomp == 5:
         _, Z, Y, X = inp.shape
         isc, isz, isy, isx = inp.stride()
@@ -251,6 +264,7 @@ def _coef(c) -> ctypes.Array:
 
 def acs_stencil_plain(u, a, out, c=None, halo: int = 4, stream=None) -> None:
     g = grid_for(u, out, halo, 1)
+    _on_device(a)
     if tuple(a.stride()) != tuple(u.stride()) or tuple(a.shape) != tuple(u.shape):
         raise ValueError("u and a must have the same shape and strides")
     _check(lib().acs_stencil_plain(u.data_ptr(), a.data_ptr(), out.data_ptr(), ctypes.byref(g), _coef(c),
@@ -259,6 +273,7 @@ def acs_stencil_plain(u, a, out, c=None, halo: int = 4, stream=None) -> None:
 
 def acs_stencil_saturated(u, a, out, c=None, halo: int = 4, tile=None, stream=None) -> None:
     g = grid_for(u, out, halo, 1)
+    _on_device(a)
     if tuple(a.stride()) != tuple(u.stride()) or tuple(a.shape) != tuple(u.shape):
         raise ValueError("u and a must have the same shape and strides")
     _check(lib().acs_stencil_saturated(u.data_ptr(), a.data_ptr(), out.data_ptr(), ctypes.byref(g), _coef(c),
@@ -301,6 +316,7 @@ def batch_items(kind: int, grids, halo: int | None = None):
     arr = (BatchItem * len(grids))()
     for q, (in0, in1, out) in enumerate(grids):
         g = grid_for(in0, out, halo, 5 if kind == KIND_RHS else 1)
+        _on_device(in1)
         arr[q] = BatchItem(in0.data_ptr(), in1.data_ptr() if in1 is not None else None, out.data_ptr(), g)
     return arr
 
@@ -319,6 +335,7 @@ def _batch_params(kind: int, params):
 
 def acs_batch_prepare(kind: int, grids, ws, tile=None, halo: int | None = None, stream=None) -> BatchPlan:
     """Validate and upload a batch; `ws` is a device tensor of >= acs_batch_workspace_bytes(n) bytes."""
+    _on_device(ws)
     items = batch_items(kind, grids, halo)
     plan = BatchPlan()
     nbytes = ws.numel() * ws.element_size()
@@ -371,6 +388,7 @@ def acs_autotune_stencil(u, a, out, c=None, halo=4, stream=None):
 
 
 def acs_autotune_batch(kind: int, grids, ws, params=None, halo=None, stream=None):
+    _on_device(ws)
     items = batch_items(kind, grids, halo)
     ptr, keep = _batch_params(kind, params)
     t, ms = Tile(), ctypes.c_float()
@@ -452,6 +470,7 @@ def acs_ranker_workspace_bytes(n: int, n_feats: int, hidden: int) -> int:
 
 def acs_ranker_train(feats, times_ms, params, ws, hidden=64, epochs=3000, lr=3e-3, seed=13006, stream=None):
     """Train the MLP on device tensors feats (n x F float32) and times_ms (n float32)."""
+    _on_device(feats, times_ms, params, ws)
     n, F = feats.shape
     _check(lib().acs_ranker_train(feats.data_ptr(), times_ms.data_ptr(), int(n), int(F), int(hidden), int(epochs),
                                   float(lr), int(seed), params.data_ptr(), ws.data_ptr(),
@@ -461,6 +480,7 @@ def acs_ranker_train(feats, times_ms, params, ws, hidden=64, epochs=3000, lr=3e-
 def acs_variant_rank(feats, params=None, hidden=64, scores_dev=None, stream=None):
     """(order fastest-first, scores) for device feats; params None = the paper's analytical cost."""
     import torch
+    _on_device(feats, params, scores_dev)
     n, F = feats.shape
     if scores_dev is None:
         scores_dev = torch.empty(n, dtype=torch.float32, device=feats.device)
@@ -478,6 +498,7 @@ BLOCK_PRM = (0.01, 1.5, 2.0, 0.75, 0.5)
 def acs_block_form(A, B, G, out, form, prm=BLOCK_PRM, halo: int = 1, stream=None) -> None:
     """Block-assembly body; A, B (25, Z, Y, X), G (Z, Y, X), out (75, nz, ny, nx) device tensors."""
     f = FORMS[form] if isinstance(form, str) else int(form)
+    _on_device(A, B, G, out)
     _, Z, Y, X = A.shape
     isc, isz, isy, isx = A.stride()
     if tuple(B.stride()) != (isc, isz, isy, isx) or tuple(G.stride()) != (isz, isy, isx) or isx != 1:
@@ -493,14 +514,15 @@ def acs_block_form(A, B, G, out, form, prm=BLOCK_PRM, halo: int = 1, stream=None
 
 
 def acs_rhs_host_workspace_bytes(U_host, R_host, halo: int = 2, slab: int = 0) -> int:
-    g = grid_for(U_host, R_host, halo, 5)
+    g = grid_for(U_host, R_host, halo, 5, host=True)
     return int(lib().acs_rhs_host_workspace_bytes(ctypes.byref(g), int(slab)))
 
 
 def acs_rhs_saturated_host(U_host, R_host, ws, gamma=1.4, eps=0.25, h=(1.0, 1.0, 1.0), halo=2, tile=None, slab=0,
                            stream=None) -> None:
     """Saturated RHS on host (CPU, ideally pinned) tensors, streamed in z-slabs through `ws` (device)."""
-    g = grid_for(U_host, R_host, halo, 5)
+    g = grid_for(U_host, R_host, halo, 5, host=True)
+    _on_device(ws)
     pr = _params(gamma, eps, h)
     _check(lib().acs_rhs_saturated_host(U_host.data_ptr(), R_host.data_ptr(), ctypes.byref(g), ctypes.byref(pr),
                                         _tile(tile), int(slab), ws.data_ptr(), ws.numel() * ws.element_size(),

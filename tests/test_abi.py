@@ -152,3 +152,22 @@ def test_tune_cache_file_errors(lib, tmp_path):
 
 def test_wait_selftest_rejects_null_output(lib):
     assert lib.acs_wait_selftest(None, None) == 1        # ACS_ERR_INVALID before any launch
+
+
+def test_binding_refuses_host_tensors_for_device_entry_points(lib):
+    """The device entry points take CUDA tensors: host tensors are refused before any call, and
+    the host-streamed entry point refuses the reverse."""
+    torch = pytest.importorskip("torch")
+    U = torch.zeros((5, 8, 8, 8), dtype=torch.float64)
+    R = torch.zeros((5, 4, 4, 4), dtype=torch.float64)
+    for fn in (binding.acs_rhs_plain, binding.acs_rhs_saturated):
+        with pytest.raises(ValueError, match="CUDA tensors"):
+            fn(U, R)
+    u = torch.zeros((12, 12, 12), dtype=torch.float64)
+    out = torch.zeros((4, 4, 4), dtype=torch.float64)
+    with pytest.raises(ValueError, match="CUDA tensors"):
+        binding.acs_stencil_saturated(u, u, out)
+    with pytest.raises(ValueError, match="CUDA tensors"):
+        binding.acs_batch_prepare(binding.KIND_STENCIL, [(u, u, out)], torch.zeros(64, dtype=torch.float64))
+    with pytest.raises(ValueError, match="CUDA tensors"):
+        binding.acs_rhs_saturated_host(U, R, torch.zeros(8, dtype=torch.float64))
