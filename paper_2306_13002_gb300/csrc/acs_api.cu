@@ -225,7 +225,11 @@ Span span_of(const double* p, int ncomp, i64 sc, int Z, i64 sz, int Y, i64 sy, i
 }
 bool overlap(Span a, Span b) { return a.lo < b.hi && b.lo < a.hi; }
 
-acs_status check_grid(const acs_grid* g, int radius, int ncomp, Geom& out) {
+// ncomp > 1: the arrays have component strides; in_comps / out_comps (default ncomp) are the
+// components the input and output arrays actually hold, for the extent checks.
+acs_status check_grid(const acs_grid* g, int radius, int ncomp, Geom& out, int in_comps = 0, int out_comps = 0) {
+    if (in_comps < 1) in_comps = ncomp;
+    if (out_comps < 1) out_comps = ncomp;
     if (!g) return fail(ACS_ERR_INVALID, "grid is NULL");
     if (g->nx < 1 || g->ny < 1 || g->nz < 1)
         return fail(ACS_ERR_INVALID, "interior sizes must be >= 1 (got %d x %d x %d)", g->nx, g->ny, g->nz);
@@ -234,12 +238,23 @@ acs_status check_grid(const acs_grid* g, int radius, int ncomp, Geom& out) {
     if (g->halo < radius) return fail(ACS_ERR_INVALID, "halo %d is smaller than the stencil radius %d", g->halo, radius);
     if (g->halo > 64) return fail(ACS_ERR_INVALID, "halo %d too large", g->halo);
     const i64 X = (i64)g->nx + 2 * g->halo, Y = (i64)g->ny + 2 * g->halo, Z = (i64)g->nz + 2 * g->halo;
+    // Products of caller strides and extents in 128 bits, so that no stride can overflow them;
+    // every array must span less than 2^62 bytes (the byte spans below then fit in 64 bits).
+    using i128 = __int128;
     if (g->in_sy < X) return fail(ACS_ERR_INVALID, "in_sy %lld < extended row length %lld", g->in_sy, X);
-    if (g->in_sz < g->in_sy * Y) return fail(ACS_ERR_INVALID, "in_sz %lld < in_sy * extended rows", g->in_sz);
-    if (ncomp > 1 && g->in_sc < g->in_sz * Z) return fail(ACS_ERR_INVALID, "in_sc %lld < in_sz * extended planes", g->in_sc);
+    if ((i128)g->in_sz < (i128)g->in_sy * Y) return fail(ACS_ERR_INVALID, "in_sz %lld < in_sy * extended rows", g->in_sz);
+    if (ncomp > 1 && (i128)g->in_sc < (i128)g->in_sz * Z)
+        return fail(ACS_ERR_INVALID, "in_sc %lld < in_sz * extended planes", g->in_sc);
     if (g->out_sy < g->nx) return fail(ACS_ERR_INVALID, "out_sy %lld < nx", g->out_sy);
-    if (g->out_sz < g->out_sy * g->ny) return fail(ACS_ERR_INVALID, "out_sz %lld < out_sy * ny", g->out_sz);
-    if (ncomp > 1 && g->out_sc < g->out_sz * g->nz) return fail(ACS_ERR_INVALID, "out_sc %lld < out_sz * nz", g->out_sc);
+    if ((i128)g->out_sz < (i128)g->out_sy * g->ny) return fail(ACS_ERR_INVALID, "out_sz %lld < out_sy * ny", g->out_sz);
+    if (ncomp > 1 && (i128)g->out_sc < (i128)g->out_sz * g->nz)
+        return fail(ACS_ERR_INVALID, "out_sc %lld < out_sz * nz", g->out_sc);
+    const i128 in_last = (i128)(in_comps - 1) * (ncomp > 1 ? g->in_sc : 0) + (i128)(Z - 1) * g->in_sz +
+                         (i128)(Y - 1) * g->in_sy + X;
+    const i128 out_last = (i128)(out_comps - 1) * (ncomp > 1 ? g->out_sc : 0) + (i128)(g->nz - 1) * g->out_sz +
+                          (i128)(g->ny - 1) * g->out_sy + g->nx;
+    if (in_last * 8 >= ((i128)1 << 62) || out_last * 8 >= ((i128)1 << 62))
+        return fail(ACS_ERR_INVALID, "array extent of 2^62 bytes or more");
     out.nx = g->nx;
     out.ny = g->ny;
     out.nz = g->nz;
@@ -440,11 +455,8 @@ acs_status acs_block_form(const double* A, const double* B, const double* G, dou
     if (form != ACS_FORM_AS_WRITTEN && form != ACS_FORM_CSE && form != ACS_FORM_CSE_BULK && form != ACS_FORM_SATURATED)
         return fail(ACS_ERR_INVALID, "block body form %d is not built", form);
     Geom geo;
-    acs_status st = check_grid(g, 1, 2, geo);
+    acs_status st = check_grid(g, 1, 2, geo, 25, 75);   // A, B: 25 components; out: 75
     if (st != ACS_OK) return st;
-    const i64 Z = (i64)geo.nz + 2 * geo.halo;
-    if (g->in_sc < g->in_sz * Z) return fail(ACS_ERR_INVALID, "in_sc too small for A/B");
-    if (g->out_sc < g->out_sz * geo.nz) return fail(ACS_ERR_INVALID, "out_sc too small");
     for (int q = 0; q < 5; ++q)
         if (!std::isfinite(prm[q])) return fail(ACS_ERR_INVALID, "parameter %d is not finite", q);
     const Span so = span_of(out, 75, geo.osc, geo.nz, geo.osz, geo.ny, geo.osy, geo.nx);

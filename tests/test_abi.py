@@ -91,6 +91,25 @@ def test_rhs_rejects_short_strides(lib):
     assert _call_rhs(lib, FAKE_U, FAKE_R, g, _params()) == 1
 
 
+@pytest.mark.parametrize("field,value", [("in_sy", 1 << 62), ("in_sz", 1 << 62), ("in_sc", (1 << 63) - 1),
+                                         ("out_sy", 1 << 61), ("out_sc", 1 << 60)])
+def test_rejects_strides_whose_extent_overflows(lib, field, value):
+    """Huge strides (products with the extents past 64 bits, or arrays of 2^62 bytes and more)
+    are rejected on the host, for both forms and the stencil."""
+    g = _grid()
+    setattr(g, field, value)
+    if field == "in_sy":
+        g.in_sz, g.in_sc = max(g.in_sz, 1 << 62), max(g.in_sc, 1 << 62)
+    assert _call_rhs(lib, FAKE_U, FAKE_R, g, _params()) == 1
+    assert _call_rhs(lib, FAKE_U, FAKE_R, g, _params(), sat=True) == 1
+    gs = _grid(halo=4, comp=False)
+    if field.endswith("sc"):
+        return
+    setattr(gs, field, value)
+    c = (ctypes.c_double * 12)(*([1.0] * 12))
+    assert lib.acs_stencil_saturated(FAKE_U, FAKE_U + 0x1000000, FAKE_R, ctypes.byref(gs), c, None, None) == 1
+
+
 def test_saturated_rejects_unbuilt_tile_and_flags(lib):
     assert _call_rhs(lib, FAKE_U, FAKE_R, _grid(), _params(), sat=True, tile=(24, 8, 0, 0)) == 4
     assert _call_rhs(lib, FAKE_U, FAKE_R, _grid(), _params(), sat=True, tile=(32, 8, 0, 4)) == 1   # unknown flag
@@ -171,3 +190,21 @@ def test_binding_refuses_host_tensors_for_device_entry_points(lib):
         binding.acs_batch_prepare(binding.KIND_STENCIL, [(u, u, out)], torch.zeros(64, dtype=torch.float64))
     with pytest.raises(ValueError, match="CUDA tensors"):
         binding.acs_rhs_saturated_host(U, R, torch.zeros(8, dtype=torch.float64))
+
+
+def test_block_form_rejects_bad_arguments(lib):
+    """The block-assembly body's host checks: NULL arrays, unknown form, short component strides,
+    an output extent past 2^62 bytes (75 components), an output overlapping A."""
+    nx = ny = nz = 8
+    X = nx + 2
+    g = binding.Grid(nx, ny, nz, 1, X, X * X, X ** 3, nx, nx * ny, nx * ny * nz)
+    prm = (ctypes.c_double * 5)(*binding.BLOCK_PRM)
+    A, B, G, OUT = 0x10000000, 0x20000000, 0x30000000, 0x40000000
+    f = binding.FORMS["saturated"]
+    assert lib.acs_block_form(None, B, G, OUT, ctypes.byref(g), prm, f, None) == 1
+    assert lib.acs_block_form(A, B, G, OUT, ctypes.byref(g), prm, 99, None) == 1
+    short = binding.Grid(nx, ny, nz, 1, X, X * X, X ** 3 - 1, nx, nx * ny, nx * ny * nz)
+    assert lib.acs_block_form(A, B, G, OUT, ctypes.byref(short), prm, f, None) == 1
+    huge = binding.Grid(nx, ny, nz, 1, X, X * X, X ** 3, nx, nx * ny, 1 << 58)
+    assert lib.acs_block_form(A, B, G, OUT, ctypes.byref(huge), prm, f, None) == 1
+    assert lib.acs_block_form(A, B, G, A + 8 * 100, ctypes.byref(g), prm, f, None) == 7   # overlaps A
