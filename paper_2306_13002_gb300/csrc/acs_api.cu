@@ -3,6 +3,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -176,15 +177,15 @@ acs_status encode_plane_map(const double* base, const Geom& g, int ncomp, int bo
 }
 
 int num_sms() {
-    static int cached[64] = {0};
+    static std::atomic<int> cached[64];   // zero-initialised (static storage); 0 = not read yet
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
-    if (cached[dev] == 0) {
-        int n = 0;
+    int n = cached[dev].load(std::memory_order_relaxed);
+    if (n == 0) {
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
-        cached[dev] = n;
+        cached[dev].store(n, std::memory_order_relaxed);
     }
-    return cached[dev];
+    return n;
 }
 
 // z-chunk per block: balance whole waves of blocks against the per-chunk warm-up (one extra
