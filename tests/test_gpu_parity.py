@@ -213,6 +213,15 @@ def test_rhs_128cubed_full(form):
     assert_parity(_rhs_gpu(form, U).cpu().numpy(), ref, what=f"rhs {form} 128^3")
 
 
+@pytest.mark.parametrize("tile", [None, (16, 16, 0, 3), (32, 8, 16, 2)])
+def test_rhs_162cubed_full(tile):
+    """The grid side of NPB class C (162^3), the size of the paper's CFD workloads: ragged for
+    every tile width (162 = 10 x 16 + 2 = 5 x 32 + 2), compared in full."""
+    U = inputs.rhs_field(162, halo=2, seed=inputs.SEED_RHS_LARGE + 1)
+    ref = oracle.rhs(U, threads=16)
+    assert_parity(_rhs_gpu("saturated", U, tile=tile).cpu().numpy(), ref, what=f"rhs saturated 162^3 {tile}")
+
+
 @pytest.mark.parametrize("form", ["plain", "saturated"])
 def test_rhs_256cubed_sampled_planes(form):
     """The benchmark workload (256^3, default launch) on sampled z-planes."""
@@ -300,6 +309,14 @@ def test_stencil_384cubed_sampled_planes(form):
         ref = oracle.stencil(u, a, k_range=(k, k + 1), threads=8)[k]
         assert_parity(out[k].cpu().numpy(), ref, what=f"stencil {form} 384^3 plane {k}")
     assert torch.isfinite(out).all()
+
+
+@pytest.mark.parametrize("tile", [None, (32, 8, 0, 1), (64, 4, 16, 2), (16, 16, 0, 3)])
+def test_stencil_130cubed_full(tile):
+    """A ragged cube for every tile width (130 = 4 x 32 + 2 = 2 x 64 + 2 = 8 x 16 + 2), in full."""
+    u, a = inputs.stencil_fields(130, seed=inputs.SEED_STENCIL + 1)
+    ref = oracle.stencil(u, a, threads=16)
+    assert_parity(_star_gpu("saturated", u, a, tile=tile).cpu().numpy(), ref, what=f"stencil 130^3 {tile}")
 
 
 def test_stencil_constant_field_zero_within_floor():
