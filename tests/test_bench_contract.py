@@ -1,0 +1,46 @@
+"""bench.py's output contract: one JSON line with the keys the benchmark driver reads.
+
+The reference arm (the CPU oracle on the host cores) runs here on the CPU; the default arm
+needs a GPU and runs a short version of the benchmark step."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _run(args, timeout):
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], capture_output=True, text=True,
+                       timeout=timeout, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout[-2000:]
+    return json.loads(lines[0])
+
+
+def test_reference_arm_line():
+    d = _run(["--impl", "reference", "--steps", "3", "--warmup", "3"], timeout=600)
+    assert d["impl"] == "reference"
+    assert d["value"] > 0 and d["unit"] == "Gpoint-updates/s" and d["higher_is_better"] is True
+    assert d["steps"] == 3 and d["warmup"] == 3 and d["ms_per_step"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"].startswith("rhs_as_written_oracle_256")
+
+
+@pytest.mark.gpu
+def test_default_arm_line():
+    d = _run(["--steps", "5", "--warmup", "3", "--no-cpu-baseline", "--no-stencil", "--no-plain"], timeout=900)
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+                "vs_baseline", "dtype", "data", "config", "roofline", "e2e", "gpu_launches", "clocks"):
+        assert key in d, key
+    assert d["n_gpus"] == 1 and d["steps"] == 5 and d["warmup"] == 3 and d["dtype"] == "f64"
+    assert d["config"]["workload"] == "rhs_saturated_256^3_fp64" and "l2" in d["config"]
+    r = d["roofline"]
+    assert r["bound"] == "alu" and 0 < r["frac"] <= 1.05 and r["achieved"] == pytest.approx(r["frac"] * r["peak"])
+    assert d["gpu_launches"] == 5
+    e = d["e2e"]
+    assert e["value"] > 0 and e["h2d_bytes_per_step"] == 703040000 and e["d2h_bytes_per_step"] == 671088640
