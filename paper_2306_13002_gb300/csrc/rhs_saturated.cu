@@ -24,7 +24,9 @@
 //    with ACS_TILE_TMA as one tensor copy per plane completing on an mbarrier), so every load
 //    of the body is issued before the arithmetic that consumes it.
 //
-// Block: BX x BY threads own a BX x BY column tile and march z over [k0, k1).
+// Block: BX x BY threads own a BX x BY column tile and march z over [k0, k1); a tile cut by
+// the grid's x edge maps its flux points (valid columns plus one halo column) to the first
+// threads, so that the warps past them stay idle (rhs_march in march.cuh).
 // Shared memory: U ring [5 slots][5 comps][BY+4][BX+4], F_x [4][BY][BX+2] (x from -1 to
 // BX), F_y [4][BY+2][BX] (y from -1 to BY). The x/y ring of fluxes just outside the tile
 // is computed by the first 2(BX+BY) threads.
