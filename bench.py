@@ -588,7 +588,8 @@ def main() -> None:
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     algo_bytes = in_bytes + out_bytes
     achieved_ops = DP_OPS_PER_POINT["rhs_saturated"] * points / (launch_ms * 1e-3) / 1e9
-    traffic = NCU_TRAFFIC.get(f"{kernel_source_hash()}:{tile_text(tuned_tile)}")
+    # the recorded figures are per 256^3 launch: other sizes report no traffic
+    traffic = NCU_TRAFFIC.get(f"{kernel_source_hash()}:{tile_text(tuned_tile)}") if n == N_RHS else None
     result = {
         "metric": METRIC,
         "value": value,
