@@ -39,19 +39,20 @@ N_STAR = 384
 # 3 energy) + 5 components x 19 (3 differences, 3 for the scaled flux sum, 10 for S2 and S1,
 # 2 for S2 - 4 S1 + 18 U, 1 final FMA) = 116. The star stencil: 1 + 12 x 2 + 1 = 26.
 DP_OPS_PER_POINT = {"rhs_saturated": 116, "star_saturated": 26}
-# Peak FP64-pipe rate: 2 operations / clock / SM (nominal 1.25 TFLOP/s of FMA at 2070 MHz on
-# 152 SMs: 1.25e12 / 2 / 152 / 2.07e9 = 1.99), i.e. 2 * 152 * 2.07e9 = 629.3 G op/s.
-SMS = 152
-SM_MAX_MHZ = 2070.0
-DP_PEAK_GOPS = 2 * SMS * SM_MAX_MHZ / 1000.0
+# The FP64 pipe's nominal issue rate: 2 operations / clock / SM (nominal 1.25 TFLOP/s of FMA
+# at 2070 MHz on 152 SMs: 1.25e12 / 2 / 152 / 2.07e9 = 1.99). The roofline's peak is the rate
+# the FP64 probe measures in the same run; 2 x SMs x max SM clock (both queried from the device)
+# is reported beside it as the derived peak. The constants are used only when a query fails.
+DP_OPS_PER_CLK_SM = 2
+FALLBACK_SMS = 152
+FALLBACK_SM_MAX_MHZ = 2070.0
 
 # DRAM bytes per launch measured by ncu, keyed by the SHA-256 of the files that define the
 # kernel and by the launch shape; a changed kernel or another shape reports null until it is
 # profiled again.
 NCU_TRAFFIC = {
     # one-pass ncu captures (dram__bytes_read.sum + dram__bytes_write.sum) of one launch at
-    # 256^3, the 4th after 3 warm-ups, in the shapes the autotuner picks; summary in
-    # profiles/bench_256_launch_list.md.
+    # 256^3, the 4th after 3 warm-ups, in the shapes the autotuner picks
     "f5e3d32491a900e9:16x16, balanced, TMA": 831502592 + 633517312,
     "f5e3d32491a900e9:32x8, balanced, TMA": 857585664 + 633793024,
 }
@@ -79,20 +80,95 @@ def measured_peaks() -> dict:
         return {}
 
 
+class Nvml:
+    """Read-only NVML queries through ctypes (libnvidia-ml ships with the driver): SM clock,
+    maximum SM clock, power and the active clock-event reasons. Nothing is set."""
+
+    CLOCK_SM = 1
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, cuda_index: int = 0):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.dev = ctypes.c_void_p()
+        ok = False
+        bus = None
+        try:
+            import torch
+            pr = torch.cuda.get_device_properties(cuda_index)
+            if hasattr(pr, "pci_bus_id"):
+                bus = "%08x:%02x:%02x.0" % (getattr(pr, "pci_domain_id", 0), pr.pci_bus_id,
+                                            getattr(pr, "pci_device_id", 0))
+        except Exception:
+            bus = None
+        if bus is not None:
+            ok = self.lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(self.dev)) == 0
+        if not ok:
+            visible = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+            idx = cuda_index
+            if visible and visible.split(",")[cuda_index].strip().isdigit():
+                idx = int(visible.split(",")[cuda_index])
+            if self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(idx), ctypes.byref(self.dev)) != 0:
+                raise RuntimeError("no NVML handle for the device")
+        self._reasons = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def _uint(self, fn, *args) -> int | None:
+        v = self.ct.c_uint()
+        return int(v.value) if fn(self.dev, *args, self.ct.byref(v)) == 0 else None
+
+    def sm_mhz(self):
+        return self._uint(self.lib.nvmlDeviceGetClockInfo, self.ct.c_int(self.CLOCK_SM))
+
+    def sm_max_mhz(self):
+        return self._uint(self.lib.nvmlDeviceGetMaxClockInfo, self.ct.c_int(self.CLOCK_SM))
+
+    def power_w(self):
+        mw = self._uint(self.lib.nvmlDeviceGetPowerUsage)
+        return None if mw is None else mw / 1000.0
+
+    def reasons(self):
+        v = self.ct.c_ulonglong()
+        if self._reasons(self.dev, self.ct.byref(v)) != 0:
+            return None
+        return sorted(name for bit, name in self.REASONS.items() if v.value & bit)
+
+
 class ClockSampler:
-    """nvidia-smi clock / throttle samples every 100 ms; keeps those inside [t0, t1]."""
+    """Samples the SM clock, power and clock-event reasons every `period_s` (in-process NVML,
+    else `nvidia-smi -lms 100`) while the bench runs; `summary` keeps the samples that fall in
+    the timed windows registered with `window(t0, t1)`."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, period_s: float = 0.004):
         self.gpu = gpu_index
-        self.samples = []
+        self.period = period_s
+        self.samples = []          # (time, sm_mhz, max_mhz, power_w, [reasons])
+        self.windows = []
         self.proc = None
         self.thread = None
+        self.stop_flag = threading.Event()
+        self.source = None
+        try:
+            self.nvml = Nvml(gpu_index)
+            self.max_mhz = self.nvml.sm_max_mhz()
+        except Exception:
+            self.nvml = None
+            self.max_mhz = None
 
     def start(self):
+        if self.nvml is not None:
+            self.source = f"NVML in-process, every {self.period * 1e3:.0f} ms"
+            self.thread = threading.Thread(target=self._poll, daemon=True)
+            self.thread.start()
+            return
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
@@ -100,33 +176,60 @@ class ClockSampler:
         except Exception:
             self.proc = None
             return
+        self.source = "nvidia-smi -lms 100"
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
 
+    def _poll(self):
+        while not self.stop_flag.is_set():
+            t = time.time()
+            try:
+                self.samples.append((t, self.nvml.sm_mhz(), self.max_mhz, self.nvml.power_w(), self.nvml.reasons()))
+            except Exception:
+                pass
+            self.stop_flag.wait(self.period)
+
     def _read(self):
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in self.proc.stdout:
-            self.samples.append((time.time(), [x.strip() for x in line.split(",")]))
+            r = [x.strip() for x in line.split(",")]
+            if len(r) < 9:
+                continue
+            num = lambda v: float(v) if v.replace(".", "").isdigit() else None  # noqa: E731
+            self.samples.append((time.time(), num(r[1]), num(r[2]), num(r[3]),
+                                 [n for n, v in zip(names, r[5:9]) if v.lower() == "active"]))
+
+    def window(self, t0: float, t1: float):
+        self.windows.append((t0, t1))
 
     def stop(self):
+        self.stop_flag.set()
         if self.proc is not None:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
 
-    def summary(self, t0: float, t1: float) -> dict:
-        rows = [s for (t, s) in self.samples if t0 <= t <= t1 and len(s) >= 9]
+    def median_mhz(self, t0: float, t1: float):
+        sm = [r[1] for r in self.samples if t0 <= r[0] <= t1 and r[1]]
+        return statistics.median(sm) if sm else None
+
+    def summary(self) -> dict:
+        rows = [r for r in self.samples if any(a <= r[0] <= b for a, b in self.windows)]
         if not rows:
-            rows = [s for (_, s) in self.samples if len(s) >= 9]
-        if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.strip().lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["no clock samples"], "samples": 0,
+                    "source": self.source}
+        sm = [r[1] for r in rows if r[1]]
+        mx = [r[2] for r in rows if r[2]] or ([self.max_mhz] if self.max_mhz else [])
+        pw = [r[3] for r in rows if r[3] is not None]
+        reasons = sorted({n for r in rows for n in (r[4] or [])})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_min_mhz": min(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(pw) if pw else None, "timed_windows": len(self.windows),
+                "source": self.source}
 
 
 def tile_text(tile) -> str:
@@ -205,6 +308,80 @@ def reduce_over_ranks(dist, x: float, op: str, device: str) -> float:
     t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def replica_throughput(dist, region_ms_local: float, steps: int, points_local: float, device: str):
+    """Weak-scaling bookkeeping of independent replicas: the job's time per step is the slowest
+    rank's (max over ranks) and its throughput the points of all ranks over that time.
+    Returns (ms per step, Gpoint-updates/s of the job, points of the job per step)."""
+    ms = reduce_over_ranks(dist, region_ms_local, "max", device) / steps
+    pts = reduce_over_ranks(dist, float(points_local), "sum", device)
+    return ms, pts / (ms * 1e-3) / 1e9, pts
+
+
+def wall_timer(fn, steps: int) -> float:
+    """Host wall-clock time of `steps` calls (ms); the timer of the CPU replicas."""
+    t = time.perf_counter()
+    for _ in range(steps):
+        fn()
+    return (time.perf_counter() - t) * 1e3
+
+
+def timed_replica_region(dist, fn, steps: int, timer, sync=lambda: None) -> float:
+    """One rank's timed region: barrier, sync, `steps` calls timed by `timer` (ms), sync,
+    barrier. Returns this rank's region time in ms."""
+    if dist:
+        dist.barrier()
+    sync()
+    ms = timer(fn, steps)
+    sync()
+    if dist:
+        dist.barrier()
+    return ms
+
+
+def launch_plan(gpus: int, env) -> str:
+    """'run' when this process is the whole job or one of `gpus` ranks, 'relaunch' when one
+    process was started for several GPUs (bench.py starts torchrun itself), else an error."""
+    if "WORLD_SIZE" in env:
+        ws = int(env["WORLD_SIZE"])
+        if ws != gpus:
+            return f"error: --gpus {gpus} but WORLD_SIZE={ws}"
+        return "run"
+    return "relaunch" if gpus > 1 else "run"
+
+
+def relaunch(args_list, gpus: int) -> int:
+    """Run this script under torch.distributed.run with one rank per GPU (127.0.0.1 rendezvous);
+    returns its exit code. Rank 0 prints the JSON line."""
+    import socket
+    sock = socket.socket()
+    sock.bind(("127.0.0.1", 0))
+    port = sock.getsockname()[1]
+    sock.close()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={gpus}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__), *args_list]
+    return subprocess.call(cmd)
+
+
+def fp64_probe(torch, binding, stream, sms: int, sampler, blocks_per_sm: int = 2, threads: int = 256,
+               iters: int = 8192, reps: int = 5) -> dict:
+    """The FP64 pipe's measured rate (acs_fp64_rate_probe: register-only FMA chains) at the RHS
+    kernel's occupancy (2 blocks of 256 threads per SM), timed with CUDA events."""
+    sink = torch.empty(sms * blocks_per_sm * threads, dtype=torch.float64, device="cuda")
+    run = lambda: binding.acs_fp64_rate_probe(sink, sms * blocks_per_sm, threads, iters, stream=stream)  # noqa: E731
+    ops = run()
+    run()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    launch_ms, _ = time_launches(torch, run, reps, stream)
+    t1 = time.time()
+    if sampler:
+        sampler.window(t0, t1)
+    gops = ops / (launch_ms * 1e-3) / 1e9
+    mhz = sampler.median_mhz(t0, t1) if sampler else None
+    return {"gops": gops, "op_per_clk_per_sm": gops * 1e3 / (mhz * sms) if mhz else None, "sm_mhz": mhz,
+            "blocks_per_sm": blocks_per_sm, "threads": threads, "ops_per_launch": ops, "launch_ms": launch_ms}
 
 
 def time_launches(torch, fn, steps: int, stream) -> tuple[float, float]:
@@ -301,7 +478,9 @@ def run_large(args) -> None:
     steps = max(3, min(args.steps, 10))
     peaks = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    out = {"study": "large workloads", "unit": UNIT}
+    sms = int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+    peak = fp64_probe(torch, binding, stream, sms, None)["gops"]
+    out = {"study": "large workloads", "unit": UNIT, "fp64_peak_measured_gops": peak}
     # ranker-picked variant: a 128-variant study at 256^3, then the pick is timed at 512^3
     small = ranker.study(n_variants=128, n_train=100, n=256, epochs=2000, reps=3)
     n = 512
@@ -331,7 +510,7 @@ def run_large(args) -> None:
         m.close()
     sat = rhs["saturated_autotuned"]["ms"]
     rhs["tile"] = list(tile)
-    rhs["fp64_frac"] = DP_OPS_PER_POINT["rhs_saturated"] * pts / (sat * 1e-3) / 1e9 / DP_PEAK_GOPS
+    rhs["fp64_frac"] = DP_OPS_PER_POINT["rhs_saturated"] * pts / (sat * 1e-3) / 1e9 / peak
     rhs["hbm_frac"] = algo_bytes / (sat * 1e-3) / 1e9 / hbm
     rhs["speedup_saturated_over_as_written"] = rhs["as_written"]["ms"] / sat
     out["rhs_512"] = rhs
@@ -357,7 +536,7 @@ def run_large(args) -> None:
         st[form] = {"ms": ms, "gpts": pts / (ms * 1e-3) / 1e9}
     sat = st["saturated_autotuned"]["ms"]
     st["tile"] = list(tile)
-    st["fp64_frac"] = DP_OPS_PER_POINT["star_saturated"] * pts / (sat * 1e-3) / 1e9 / DP_PEAK_GOPS
+    st["fp64_frac"] = DP_OPS_PER_POINT["star_saturated"] * pts / (sat * 1e-3) / 1e9 / peak
     st["hbm_frac"] = algo_bytes / (sat * 1e-3) / 1e9 / hbm
     st["speedup_saturated_over_as_written"] = st["as_written"]["ms"] / sat
     out["stencil_768"] = st
@@ -389,6 +568,12 @@ def main() -> None:
     if args.impl == "reference":
         run_reference(args)
         return
+    plan = launch_plan(args.gpus, os.environ)
+    if plan == "relaunch":
+        sys.exit(relaunch(sys.argv[1:], args.gpus))
+    if plan != "run":
+        print(plan, file=sys.stderr)
+        sys.exit(2)
     if args.large:
         run_large(args)
         return
@@ -411,7 +596,11 @@ def main() -> None:
         print(json.dumps({"study": "learned variant ranker", "metric": "chosen-variant time / measured best",
                           "unit": "ratio", **res}))
         return
+    run_ours(args)
 
+
+def run_ours(args) -> None:
+    """The step benchmark: one replica per rank (torchrun sets RANK / WORLD_SIZE)."""
     import torch
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -429,16 +618,9 @@ def main() -> None:
     if dist:
         dist.barrier()
     binding.lib()
-
-    def barrier():
-        if dist:
-            dist.barrier()
-
-    def max_over_ranks(x: float) -> float:
-        return reduce_over_ranks(dist, x, "max", "cuda")
-
-    def sum_over_ranks(x: float) -> float:
-        return reduce_over_ranks(dist, x, "sum", "cuda")
+    sync = torch.cuda.synchronize
+    props = torch.cuda.get_device_properties(local)
+    sms = int(getattr(props, "multi_processor_count", 0)) or FALLBACK_SMS
 
     n = args.n
     U_host = inputs.rhs_field(n, halo=2, seed=inputs.SEED_RHS_LARGE + rank)
@@ -450,6 +632,9 @@ def main() -> None:
     points = n ** 3
     in_bytes = U.numel() * 8
     out_bytes = R.numel() * 8
+
+    def timer(fn, steps):               # CUDA events on the launching stream
+        return time_launches(torch, fn, steps, stream)[1]
 
     sat = lambda: binding.acs_rhs_saturated(U, R, stream=stream)  # noqa: E731
     plain = lambda: binding.acs_rhs_plain(U, R, stream=stream)  # noqa: E731
@@ -463,37 +648,47 @@ def main() -> None:
         tuned_tile, _ = binding.acs_autotune_rhs(U, R, stream=stream)
     for _ in range(args.warmup):
         sat()
-    torch.cuda.synchronize()
+    sync()
 
-    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    sampler = ClockSampler(local) if rank == 0 else None
     if sampler:
         sampler.start()
-        time.sleep(0.3)
-    barrier()
-    torch.cuda.synchronize()
+        time.sleep(0.2)
+    # The FP64 pipe's measured rate, the roofline's denominator (same process, same clocks).
+    probe = fp64_probe(torch, binding, stream, sms, sampler)
+
+    if dist:
+        dist.barrier()
+    sync()
     t0 = time.time()
     launch_ms, region_ms = time_launches(torch, sat, args.steps, stream)
     t1 = time.time()
-    torch.cuda.synchronize()
-    barrier()
-    region_ms = max_over_ranks(region_ms)
-    launch_ms = max_over_ranks(launch_ms)
-    ms_per_step = region_ms / args.steps
-    value = sum_over_ranks(points / (ms_per_step * 1e-3) / 1e9)
+    sync()
+    if dist:
+        dist.barrier()
+    if sampler:
+        sampler.window(t0, t1)
+    launch_ms = reduce_over_ranks(dist, launch_ms, "max", "cuda")
+    ms_per_step, value, _ = replica_throughput(dist, region_ms, args.steps, points, "cuda")
+    main_mhz = sampler.median_mhz(t0, t1) if sampler else None
+
+    def timed(fn, steps):
+        """(ms per step, job Gpoint/s) of a timed leg, its window registered with the sampler."""
+        ta = time.time()
+        rm = timed_replica_region(dist, fn, steps, timer, sync)
+        if sampler:
+            sampler.window(ta, time.time())
+        ms, val, _ = replica_throughput(dist, rm, steps, points, "cuda")
+        return ms, val
 
     # As-written form on the same input.
     as_written = None
     if not args.no_plain:
         for _ in range(2):
             plain()
-        torch.cuda.synchronize()
-        plain_steps = max(3, min(args.steps, 40))
-        barrier()
-        plain_launch_ms, plain_region_ms = time_launches(torch, plain, plain_steps, stream)
-        barrier()
-        plain_ms = max_over_ranks(plain_region_ms) / plain_steps
-        plain_value = sum_over_ranks(points / (plain_ms * 1e-3) / 1e9)
-        as_written = {"value": plain_value, "ms_per_step": plain_ms, "launch_ms": plain_launch_ms,
+        sync()
+        plain_ms, plain_value = timed(plain, max(3, min(args.steps, 40)))
+        as_written = {"value": plain_value, "ms_per_step": plain_ms,
                       "speedup_saturated_over_as_written": plain_ms / ms_per_step}
 
     # The paper's ablation ladder on the same input (Sec. VII code versions).
@@ -504,13 +699,9 @@ def main() -> None:
             fn = lambda f=form: binding.acs_rhs_form(U, R, f, stream=stream)  # noqa: E731
             for _ in range(2):
                 fn()
-            torch.cuda.synchronize()
-            steps_f = max(3, min(args.steps, 40))
-            barrier()
-            lm, rm = time_launches(torch, fn, steps_f, stream)
-            barrier()
-            ms = max_over_ranks(rm) / steps_f
-            ladder[form] = {"ms": ms, "value": sum_over_ranks(points / (ms * 1e-3) / 1e9)}
+            sync()
+            ms, val = timed(fn, max(3, min(args.steps, 40)))
+            ladder[form] = {"ms": ms, "value": val}
         if as_written:
             ladder["as_written"] = {"ms": as_written["ms_per_step"], "value": as_written["value"]}
         ladder["saturated"] = {"ms": ms_per_step, "value": value}
@@ -523,13 +714,9 @@ def main() -> None:
                              device="cuda")
         e2e_step = lambda: binding.acs_rhs_saturated_host(U_pin, R_pin, ws_e2e, stream=stream)  # noqa: E731
         e2e_step()
-        torch.cuda.synchronize()
+        sync()
         e2e_steps = max(3, min(args.steps, 20))
-        barrier()
-        _, e2e_region = time_launches(torch, e2e_step, e2e_steps, stream)
-        barrier()
-        e2e_ms = max_over_ranks(e2e_region) / e2e_steps
-        e2e_value = sum_over_ranks(points / (e2e_ms * 1e-3) / 1e9)
+        e2e_ms, e2e_value = timed(e2e_step, e2e_steps)
 
         def serial_step():   # for comparison: upload, kernel, download in sequence on one stream
             U.copy_(U_pin, non_blocking=True)
@@ -537,18 +724,12 @@ def main() -> None:
             R_pin.copy_(R, non_blocking=True)
 
         serial_step()
-        torch.cuda.synchronize()
+        sync()
         _, ser_region = time_launches(torch, serial_step, e2e_steps, stream)
         e2e = {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_ms, "h2d_bytes_per_step": in_bytes,
                "d2h_bytes_per_step": out_bytes, "entry_point": "acs_rhs_saturated_host (pinned host U, R)",
                "serial_copy_kernel_copy_ms": ser_region / e2e_steps}
         del ws_e2e
-
-    if sampler:
-        sampler.stop()
-        clocks = sampler.summary(t0, t1)
-    else:
-        clocks = None
 
     # Star stencil, both forms, as context (one replica per rank, rank 0 reports).
     stencil = None
@@ -566,19 +747,34 @@ def main() -> None:
         for name, fn in (("saturated", ssat), ("as_written", splain)):
             for _ in range(3):
                 fn()
-            torch.cuda.synchronize()
-            lm, rm = time_launches(torch, fn, max(3, min(args.steps, 50)), stream)
-            ms = rm / max(3, min(args.steps, 50))
-            res[name] = {"ms": ms, "gpts": m ** 3 / (ms * 1e-3) / 1e9}
+            sync()
+            k = max(3, min(args.steps, 50))
+            ta = time.time()
+            lm, rm = time_launches(torch, fn, k, stream)
+            if sampler:
+                sampler.window(ta, time.time())
+            res[name] = {"ms": rm / k, "gpts": m ** 3 / (rm / k * 1e-3) / 1e9}
         star_bytes = 8 * (2 * (m + 8) ** 3 + m ** 3)
         res["speedup"] = res["as_written"]["ms"] / res["saturated"]["ms"]
-        res["saturated"]["fp64_gops"] = DP_OPS_PER_POINT["star_saturated"] * m ** 3 / (res["saturated"]["ms"] * 1e-3) / 1e9
+        star_gops = DP_OPS_PER_POINT["star_saturated"] * m ** 3 / (res["saturated"]["ms"] * 1e-3) / 1e9
+        res["saturated"]["fp64_gops"] = star_gops
+        res["saturated"]["fp64_frac"] = star_gops / probe["gops"]
         res["saturated"]["hbm_gbs_algorithmic"] = star_bytes / (res["saturated"]["ms"] * 1e-3) / 1e9
         stencil = {"grid": [m] * 3, "halo": 4, **res}
         del u, a, out
         torch.cuda.empty_cache()
         stencil["batch64"] = bench_batch(torch, binding, inputs, stream, max(3, min(args.steps, 50)))
+        b = stencil["batch64"]["graph_autotuned"]
+        b["fp64_frac"] = DP_OPS_PER_POINT["star_saturated"] * stencil["batch64"]["points"] / (b["ms"] * 1e-3) / 1e9 \
+            / probe["gops"]
 
+    if sampler:
+        sampler.stop()
+        clocks = sampler.summary()
+        max_mhz = clocks.get("sm_max_mhz") or sampler.max_mhz
+    else:
+        clocks = None
+        max_mhz = None
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -588,6 +784,8 @@ def main() -> None:
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     algo_bytes = in_bytes + out_bytes
     achieved_ops = DP_OPS_PER_POINT["rhs_saturated"] * points / (launch_ms * 1e-3) / 1e9
+    derived = DP_OPS_PER_CLK_SM * sms * (max_mhz or FALLBACK_SM_MAX_MHZ) / 1000.0
+    peak = probe["gops"]
     # the recorded figures are per 256^3 launch: other sizes report no traffic
     traffic = NCU_TRAFFIC.get(f"{kernel_source_hash()}:{tile_text(tuned_tile)}") if n == N_RHS else None
     result = {
@@ -606,9 +804,17 @@ def main() -> None:
         "config": {"workload": f"rhs_saturated_{n}^3_fp64", "grid": [n] * 3, "halo": 2, "gamma": 1.4, "eps": 0.25,
                    "tile": tile_text(tuned_tile) + ("" if args.tile else " (acs_autotune_rhs)"), "l2": f"inputs larger than L2 ({in_bytes / 1e6:.0f} MB in, {out_bytes / 1e6:.0f} MB out)",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "alu", "achieved": achieved_ops, "peak": DP_PEAK_GOPS, "unit": "G FP64-pipe op/s",
-                     "frac": achieved_ops / DP_PEAK_GOPS, "traffic": traffic,
-                     "peak_source": "derived: 2 FP64 op/clk/SM x 152 SMs x 2070 MHz"},
+        "roofline": {"bound": "alu", "achieved": achieved_ops, "peak": peak, "unit": "G FP64-pipe op/s",
+                     "frac": achieved_ops / peak, "traffic": traffic,
+                     "peak_source": "measured in this run: acs_fp64_rate_probe, register-only FP64 FMA chains at "
+                                    f"{probe['blocks_per_sm']} blocks x {probe['threads']} threads per SM",
+                     "peak_derived": derived,
+                     "peak_derived_source": f"{DP_OPS_PER_CLK_SM} FP64 op/clk/SM x {sms} SMs (queried) x "
+                                            f"{max_mhz or FALLBACK_SM_MAX_MHZ:.0f} MHz max SM clock "
+                                            f"({'NVML' if max_mhz else 'fallback'})",
+                     "frac_of_derived": achieved_ops / derived,
+                     "sm_mhz_during_kernel": main_mhz},
+        "fp64_probe": probe,
         "hbm": {"algorithmic_bytes_per_launch": algo_bytes, "achieved_gbs": algo_bytes / (launch_ms * 1e-3) / 1e9,
                 "peak_gbs": hbm_peak, "frac": algo_bytes / (launch_ms * 1e-3) / 1e9 / hbm_peak,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6800"},

@@ -262,10 +262,13 @@ acs_status acs_batch_launch(const acs_batch_plan *plan, const void *params, acs_
  * in a fixed device array inside the library, sized for ACS_BATCH_STATIC_MAX grids, held on
  * every GPU that loads the library until the process exits. n > ACS_BATCH_STATIC_MAX
  * returns ACS_ERR_WORKSPACE without launching. The first call on a device looks up the
- * array's device address with that device current; make that first call before any stream
- * capture. Every call uploads the unit table (synchronising `stream`, as acs_batch_prepare
- * does), zeroes the counter and launches; calls share the array, so calls whose work
- * overlaps on the GPU race. `tile` NULL = 32 x 8, z-chunks of 16; `params` as for the kind.
+ * array's device address with that device current. Every call uploads the unit table with a
+ * host copy and synchronises `stream` (as acs_batch_prepare does), then zeroes the counter and
+ * launches, so no call can be made while `stream` is being captured into a CUDA graph: callers
+ * that want a graph use acs_batch_prepare + acs_batch_launch. Calls from several host threads
+ * are serialised from upload to launch by a library mutex; calls share the array, so calls
+ * whose kernels overlap on the GPU (streams not ordered against each other) race.
+ * `tile` NULL = 32 x 8, z-chunks of 16; `params` as for the kind.
  */
 #define ACS_BATCH_STATIC_MAX 256
 acs_status acs_batch_run_static(const acs_batch_item *items, int n, int kind, const acs_tile *tile,
@@ -335,10 +338,18 @@ size_t acs_ranker_param_count(int n_feats, int hidden);
 size_t acs_ranker_workspace_bytes(int n, int n_feats, int hidden);
 /* Train on n variants: feats (device, n x n_feats floats), times_ms (device, n floats > 0);
  * writes the model into params (device, acs_ranker_param_count floats). Full-batch Adam on
- * the squared error of the standardised log time; deterministic for a given seed. */
+ * the squared error of the standardised log time; deterministic for a given seed. epochs == 0
+ * writes the initial model only (standardisation statistics and seeded initial weights).
+ * Parameter layout (floats): mu[F] sd[F] tmu tsd W1[H][F] b1[H] W2[H][H] b2[H] w3[H] b3. */
 acs_status acs_ranker_train(const float *feats, const float *times_ms, int n, int n_feats, int hidden, int epochs,
                             float lr, unsigned long long seed, float *params, void *ws, size_t ws_bytes,
                             acs_stream stream);
+/* Gradient of the training loss (mean squared error of the standardised log time, with the
+ * statistics stored in params) with respect to every parameter at `params`, without updating
+ * them: grad (device, acs_ranker_param_count floats; 0 for mu, sd, tmu, tsd). Same kernels as
+ * one training epoch. ws as for acs_ranker_train. Synchronises `stream`. */
+acs_status acs_ranker_gradient(const float *feats, const float *times_ms, int n, int n_feats, int hidden,
+                               const float *params, float *grad, void *ws, size_t ws_bytes, acs_stream stream);
 typedef struct acs_ranker_model {
     int n_feats;
     int hidden;
@@ -349,6 +360,13 @@ typedef struct acs_ranker_model {
  * cost feats[i][0] when model is NULL). Synchronises `stream`. */
 acs_status acs_variant_rank(const float *feats, int n, int n_feats, const acs_ranker_model *model, float *scores_dev,
                             int *order_out, float *score_out, acs_stream stream);
+/* Save a trained model to a small versioned text file ("acs-ranker-model 1", then "F H P",
+ * then the P parameters in hexadecimal floating point, so a load restores the same bits), and
+ * load one back into device memory: params (device) of `capacity` floats, or NULL to read
+ * only n_feats / hidden (either may be NULL). ACS_ERR_INVALID for an unreadable or malformed
+ * file, ACS_ERR_WORKSPACE if the buffer is too small. Synchronous. */
+acs_status acs_ranker_save(const char *path, const acs_ranker_model *model);
+acs_status acs_ranker_load(const char *path, float *params, size_t capacity, int *n_feats, int *hidden);
 
 /*
  * acs_block_form - the block-assembly body (a third loop body, the many-statement shape of
@@ -387,6 +405,25 @@ acs_status acs_wait_timeouts(unsigned int *count);
  * timeouts, ACS_ERR_CUDA if the launch or the read fails.
  */
 acs_status acs_wait_selftest(unsigned int *timeouts, acs_stream stream);
+
+/*
+ * acs_fp64_rate_probe - measure the FP64 pipe: `blocks` x `threads` threads (threads a multiple
+ * of 32, at most 1024) each run 8 independent chains of `iters` dependent FMAs whose three
+ * operands are registers (the form every FP64 operation of the saturated kernels takes), and
+ * store one double each into sink (device, blocks x threads doubles). *ops receives the FP64
+ * operations the launch issues (blocks x threads x iters x 8); the caller times the launch on
+ * `stream` (CUDA events) to get the pipe's rate, the denominator of the saturated kernels'
+ * roofline. Asynchronous.
+ */
+acs_status acs_fp64_rate_probe(double *sink, int blocks, int threads, int iters, long long *ops, acs_stream stream);
+
+/*
+ * acs_rcp_selftest - apply the saturated RHS's reciprocal to n device doubles: y[i] ~ 1/x[i]
+ * (a hardware estimate refined by one third-order Newton-Raphson step for normal |x| in
+ * [2^-1000, 2^1001), an IEEE division otherwise). For measuring its error against 1/x.
+ * Asynchronous; x and y must not overlap.
+ */
+acs_status acs_rcp_selftest(const double *x, double *y, long long n, acs_stream stream);
 
 /* Reason for the calling thread's most recent failed call ("" if none). */
 const char *acs_last_error(void);

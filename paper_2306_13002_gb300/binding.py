@@ -82,7 +82,8 @@ EXPORTS = ("acs_rhs_plain", "acs_rhs_saturated", "acs_rhs_form", "acs_stencil_pl
            "acs_variant_build", "acs_variant_launch", "acs_variant_free", "acs_ranker_param_count",
            "acs_ranker_workspace_bytes", "acs_ranker_train", "acs_variant_rank", "acs_status_string",
            "acs_last_error", "acs_abi_version", "acs_block_form", "acs_rhs_host_workspace_bytes",
-           "acs_rhs_saturated_host", "acs_wait_timeouts", "acs_wait_selftest")
+           "acs_rhs_saturated_host", "acs_wait_timeouts", "acs_wait_selftest", "acs_ranker_gradient",
+           "acs_ranker_save", "acs_ranker_load", "acs_fp64_rate_probe", "acs_rcp_selftest")
 
 
 def lib() -> ctypes.CDLL:
@@ -158,6 +159,15 @@ def lib() -> ctypes.CDLL:
             L.acs_wait_timeouts.restype = st
             L.acs_wait_selftest.argtypes = [ctypes.POINTER(ctypes.c_uint), ctypes.c_void_p]
             L.acs_wait_selftest.restype = st
+            L.acs_ranker_gradient.argtypes = [p, p, st, st, st, p, p, p, ctypes.c_size_t, p]
+            L.acs_ranker_save.argtypes = [ctypes.c_char_p, ctypes.POINTER(RankerModel)]
+            L.acs_ranker_load.argtypes = [ctypes.c_char_p, p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int)]
+            L.acs_fp64_rate_probe.argtypes = [p, st, st, st, ctypes.POINTER(ctypes.c_longlong), p]
+            L.acs_rcp_selftest.argtypes = [p, p, ctypes.c_longlong, p]
+            for f in ("acs_ranker_gradient", "acs_ranker_save", "acs_ranker_load", "acs_fp64_rate_probe",
+                      "acs_rcp_selftest"):
+                getattr(L, f).restype = st
             _lib = L
     return _lib
 
@@ -360,8 +370,9 @@ def acs_batch_run_static(kind: int, grids, params=None, tile=None, halo: int | N
     For callers that cannot allocate device memory when they run a batch (a fixed budget
     handed out by their own allocator, or a loop that cannot accept an allocation's
     synchronisation). At most BATCH_STATIC_MAX grids; calls share the scratch, so calls
-    that overlap on the GPU race. The first call on a device sets up the scratch address;
-    make it before any stream capture.
+    whose kernels overlap on the GPU race. Every call synchronises the stream (it uploads
+    the unit table), so it cannot run inside a CUDA-graph capture; use acs_batch_prepare and
+    acs_batch_launch for a graph.
     """
     items = batch_items(kind, grids, halo)
     ptr, keep = _batch_params(kind, params)
@@ -490,6 +501,52 @@ def acs_variant_rank(feats, params=None, hidden=64, scores_dev=None, stream=None
     _check(lib().acs_variant_rank(feats.data_ptr(), int(n), int(F), ctypes.byref(model) if model else None,
                                   scores_dev.data_ptr(), order, score, _stream_ptr(stream)), "acs_variant_rank")
     return list(order), list(score)
+
+
+def acs_ranker_gradient(feats, times_ms, params, grad, ws, hidden=64, stream=None) -> None:
+    """Loss gradient at `params` (no update) into the device tensor `grad` (P floats)."""
+    _on_device(feats, times_ms, params, grad, ws)
+    n, F = feats.shape
+    _check(lib().acs_ranker_gradient(feats.data_ptr(), times_ms.data_ptr(), int(n), int(F), int(hidden),
+                                     params.data_ptr(), grad.data_ptr(), ws.data_ptr(),
+                                     ws.numel() * ws.element_size(), _stream_ptr(stream)), "acs_ranker_gradient")
+
+
+def acs_ranker_save(path: str, params, n_feats: int, hidden: int = 64) -> None:
+    _on_device(params)
+    model = RankerModel(int(n_feats), int(hidden), params.data_ptr())
+    _check(lib().acs_ranker_save(str(path).encode(), ctypes.byref(model)), "acs_ranker_save")
+
+
+def acs_ranker_load(path: str, device="cuda"):
+    """(params device tensor, n_feats, hidden) from a model file written by acs_ranker_save."""
+    import torch
+    F, H = ctypes.c_int(), ctypes.c_int()
+    _check(lib().acs_ranker_load(str(path).encode(), None, 0, ctypes.byref(F), ctypes.byref(H)), "acs_ranker_load")
+    params = torch.empty(acs_ranker_param_count(F.value, H.value), dtype=torch.float32, device=device)
+    _check(lib().acs_ranker_load(str(path).encode(), params.data_ptr(), params.numel(), None, None),
+           "acs_ranker_load")
+    return params, F.value, H.value
+
+
+def acs_fp64_rate_probe(sink, blocks: int, threads: int, iters: int, stream=None) -> int:
+    """Launch the FP64-pipe probe (asynchronous); returns the FP64 operations it issues."""
+    _on_device(sink)
+    if sink.numel() < blocks * threads:
+        raise ValueError("sink holds fewer than blocks x threads doubles")
+    ops = ctypes.c_longlong()
+    _check(lib().acs_fp64_rate_probe(sink.data_ptr(), int(blocks), int(threads), int(iters), ctypes.byref(ops),
+                                     _stream_ptr(stream)), "acs_fp64_rate_probe")
+    return int(ops.value)
+
+
+def acs_rcp_selftest(x, y, stream=None) -> None:
+    """y = the saturated RHS's reciprocal of x (device float64 tensors of equal size)."""
+    _on_device(x, y)
+    if x.numel() != y.numel() or not x.is_contiguous() or not y.is_contiguous():
+        raise ValueError("x and y must be contiguous and of equal size")
+    _check(lib().acs_rcp_selftest(x.data_ptr(), y.data_ptr(), int(x.numel()), _stream_ptr(stream)),
+           "acs_rcp_selftest")
 
 
 BLOCK_PRM = (0.01, 1.5, 2.0, 0.75, 0.5)

@@ -622,7 +622,7 @@ acs_status acs_ranker_train(const float* feats, const float* times_ms, int n, in
                             float lr, unsigned long long seed, float* params, void* ws, size_t ws_bytes,
                             acs_stream stream) {
     if (!feats || !times_ms || !params || !ws) return fail(ACS_ERR_INVALID, "NULL pointer");
-    if (n < 2 || n_feats < 1 || n_feats > 1024 || hidden < 1 || hidden > 1024 || epochs < 1 || !(lr > 0.f))
+    if (n < 2 || n_feats < 1 || n_feats > 1024 || hidden < 1 || hidden > 1024 || epochs < 0 || !(lr > 0.f))
         return fail(ACS_ERR_INVALID, "bad ranker training size or rate");
     if (!aligned(ws, 16) || !aligned(params, 4) || !aligned(feats, 4)) return fail(ACS_ERR_ALIGN, "misaligned buffer");
     return ranker_train(feats, times_ms, n, n_feats, hidden, epochs, lr, seed, params, ws, ws_bytes,
@@ -658,6 +658,48 @@ acs_status acs_variant_rank(const float* feats, int n, int n_feats, const acs_ra
     if (score_out)
         for (int i = 0; i < n; ++i) score_out[i] = sc[i];
     return ACS_OK;
+}
+
+acs_status acs_ranker_gradient(const float* feats, const float* times_ms, int n, int n_feats, int hidden,
+                               const float* params, float* grad, void* ws, size_t ws_bytes, acs_stream stream) {
+    if (!feats || !times_ms || !params || !grad || !ws) return fail(ACS_ERR_INVALID, "NULL pointer");
+    if (n < 1 || n_feats < 1 || n_feats > 1024 || hidden < 1 || hidden > 1024)
+        return fail(ACS_ERR_INVALID, "bad ranker sizes");
+    if (!aligned(ws, 16) || !aligned(params, 4) || !aligned(feats, 4) || !aligned(grad, 4))
+        return fail(ACS_ERR_ALIGN, "misaligned buffer");
+    return ranker_gradient(feats, times_ms, n, n_feats, hidden, params, grad, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+acs_status acs_ranker_save(const char* path, const acs_ranker_model* model) {
+    if (!path || !model || !model->params) return fail(ACS_ERR_INVALID, "NULL path or model");
+    if (model->n_feats < 1 || model->n_feats > 1024 || model->hidden < 1 || model->hidden > 1024)
+        return fail(ACS_ERR_INVALID, "bad model sizes");
+    return ranker_save(path, model->params, model->n_feats, model->hidden);
+}
+
+acs_status acs_ranker_load(const char* path, float* params, size_t capacity, int* n_feats, int* hidden) {
+    if (!path) return fail(ACS_ERR_INVALID, "path is NULL");
+    if (params && !aligned(params, 4)) return fail(ACS_ERR_ALIGN, "misaligned buffer");
+    return ranker_load(path, params, capacity, n_feats, hidden);
+}
+
+acs_status acs_fp64_rate_probe(double* sink, int blocks, int threads, int iters, long long* ops, acs_stream stream) {
+    if (!sink) return fail(ACS_ERR_INVALID, "sink is NULL");
+    if (blocks < 1 || threads < 32 || threads > 1024 || threads % 32 != 0 || iters < 1)
+        return fail(ACS_ERR_INVALID, "bad probe size (blocks %d, threads %d, iters %d)", blocks, threads, iters);
+    if (!aligned(sink, 8)) return fail(ACS_ERR_ALIGN, "sink must be 8-byte aligned");
+    if (ops) *ops = fp64_probe_ops(blocks, threads, iters);
+    return launch_fp64_probe(sink, blocks, threads, iters, (cudaStream_t)stream);
+}
+
+acs_status acs_rcp_selftest(const double* x, double* y, long long n, acs_stream stream) {
+    if (n < 0 || n > (1ll << 58)) return fail(ACS_ERR_INVALID, "n must be in [0, 2^58]");
+    if (n == 0) return ACS_OK;
+    if (!x || !y) return fail(ACS_ERR_INVALID, "x or y is NULL");
+    if (!aligned(x, 8) || !aligned(y, 8)) return fail(ACS_ERR_ALIGN, "x and y must be 8-byte aligned");
+    const Span sx{(uintptr_t)x, (uintptr_t)x + 8 * (uintptr_t)n}, sy{(uintptr_t)y, (uintptr_t)y + 8 * (uintptr_t)n};
+    if (overlap(sx, sy)) return fail(ACS_ERR_ALIAS, "y overlaps x");
+    return launch_rcp_selftest(x, y, n, (cudaStream_t)stream);
 }
 
 acs_status acs_tune_cache_save(const char* path) {
@@ -713,6 +755,6 @@ acs_status acs_wait_selftest(unsigned int* timeouts, acs_stream stream) {
     return ACS_OK;
 }
 
-int acs_abi_version(void) { return 102; }
+int acs_abi_version(void) { return 103; }
 
 }  // extern "C"

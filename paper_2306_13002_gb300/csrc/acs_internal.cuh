@@ -88,6 +88,15 @@ acs_status ranker_train(const float* feats, const float* times, int n, int F, in
 acs_status ranker_predict(const float* feats, int n, int F, int H, const float* params, float* scores, cudaStream_t s);
 acs_status analytical_scores(const float* feats, int n, int F, float* scores, cudaStream_t s);
 acs_status ranker_denormalise(const float* params, int F, int H, std::vector<float>& y);
+acs_status ranker_gradient(const float* feats, const float* times, int n, int F, int H, const float* params,
+                           float* grad, void* ws, size_t ws_bytes, cudaStream_t s);
+acs_status ranker_save(const char* path, const float* params, int F, int H);
+acs_status ranker_load(const char* path, float* params, size_t capacity, int* F, int* H);
+
+// Probes (probe.cu).
+long long fp64_probe_ops(int blocks, int threads, int iters);
+acs_status launch_fp64_probe(double* sink, int blocks, int threads, int iters, cudaStream_t s);
+acs_status launch_rcp_selftest(const double* x, double* y, i64 n, cudaStream_t s);
 
 // Shared-memory bytes and legality of a saturated tile.
 bool rhs_tile_supported(int bx, int by);

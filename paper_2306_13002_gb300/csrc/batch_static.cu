@@ -13,8 +13,12 @@
 // host-side shadow); the device address is fetched once per device with
 // cudaGetSymbolAddress, with that device current, on the first call made on the device.
 // All calls share the one array: the work counter is zeroed on the stream before every
-// launch and the unit table is rewritten by every call, and two calls whose work overlaps
-// on the GPU race on the array.
+// launch and the unit table is rewritten by every call. A library mutex is held from the
+// upload of a call's unit table until its kernel is enqueued, so calls made from several host
+// threads at once each launch on their own table; two calls whose kernels overlap on the GPU
+// (different streams, no ordering between them) still race on the array. Each call
+// synchronises its stream (the table upload), so it cannot be made while the stream is being
+// captured into a CUDA graph.
 #include <mutex>
 
 #include "acs_internal.cuh"
@@ -30,7 +34,8 @@ constexpr size_t kStaticBytes = 64 + 112 * (size_t)kStaticMaxGrids + 8 * (size_t
 
 static __device__ __align__(256) unsigned char g_batch_scratch[kStaticBytes];
 
-std::mutex g_static_mu;
+std::mutex g_static_mu;                  // guards g_static_ptr
+std::mutex g_static_run_mu;              // held from a call's table upload to its launch
 unsigned char* g_static_ptr[64] = {nullptr};
 
 // Device address of g_batch_scratch on the current device (set up on first use).
@@ -61,6 +66,7 @@ acs_status batch_run_static(const acs_batch_item* items, const Geom* geo, int n,
     unsigned char* ws = nullptr;
     acs_status st = static_scratch(&ws);
     if (st != ACS_OK) return st;
+    std::lock_guard<std::mutex> lk(g_static_run_mu);
     BatchPlanHost plan;
     st = batch_prepare_host(items, geo, n, kind, tile, ws, kStaticBytes, s, plan);
     if (st != ACS_OK) return st;

@@ -16,7 +16,9 @@
 // sums its gradient over the samples in a fixed order, so training is deterministic).
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <numeric>
+#include <string>
 #include <vector>
 
 #include "acs_internal.cuh"
@@ -101,12 +103,18 @@ __global__ void mlp_backward_sample(const float* __restrict__ T, const float* __
     }
 }
 
+// Gradient of the loss with respect to parameter p (a thread per parameter, samples summed in
+// order), then either the Adam update of p (grad == NULL) or the gradient stored in grad[p].
 __global__ void mlp_grad_adam(const float* __restrict__ X, const float* __restrict__ H1, const float* __restrict__ H2,
                               const float* __restrict__ DH1, const float* __restrict__ DH2, const float* __restrict__ DY,
-                              float* prm, float* m, float* v, int F, int H, int n, int step, float lr) {
+                              float* prm, float* m, float* v, int F, int H, int n, int step, float lr, float* grad) {
     const Layout L(F, H);
     const size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (p < L.W1 || p >= L.P) return;  // mu, sd, tmu, tsd are fixed
+    if (p >= L.P) return;
+    if (p < L.W1) {  // mu, sd, tmu, tsd are fixed
+        if (grad) grad[p] = 0.f;
+        return;
+    }
     float g = 0.f;
     if (p < L.b1) {
         const int j = (int)((p - L.W1) / F), f = (int)((p - L.W1) % F);
@@ -128,6 +136,10 @@ __global__ void mlp_grad_adam(const float* __restrict__ X, const float* __restri
         for (int s = 0; s < n; ++s) g += DY[s] * H2[(size_t)s * H + k];
     } else {
         for (int s = 0; s < n; ++s) g += DY[s];
+    }
+    if (grad) {
+        grad[p] = g;
+        return;
     }
     const float b1 = 0.9f, b2 = 0.999f;
     const float mm = b1 * m[p] + (1.f - b1) * g;
@@ -222,12 +234,88 @@ acs_status ranker_train(const float* feats, const float* times, int n, int F, in
     const int tb = H < 32 ? 32 : ((H + 31) / 32) * 32;
     const size_t sh_f = sizeof(float) * (F + 2 * H), sh_b = sizeof(float) * H;
     const unsigned pg = (unsigned)((L.P + 255) / 256);
-    for (int e = 1; e <= epochs; ++e) {
+    for (int e = 1; e <= epochs; ++e) {   // epochs == 0: the initial model only
         mlp_forward<<<n, tb, sh_f, s>>>(feats, params, F, H, w.H1, w.H2, w.Y, 1);
         mlp_backward_sample<<<n, tb, sh_b, s>>>(w.T, params, F, H, n, w.H1, w.H2, w.Y, w.DH1, w.DH2, w.DY);
-        mlp_grad_adam<<<pg, 256, 0, s>>>(feats, w.H1, w.H2, w.DH1, w.DH2, w.DY, params, w.m, w.v, F, H, n, e, lr);
+        mlp_grad_adam<<<pg, 256, 0, s>>>(feats, w.H1, w.H2, w.DH1, w.DH2, w.DY, params, w.m, w.v, F, H, n, e, lr,
+                                         nullptr);
     }
     return launch_status("ranker training kernels");
+}
+
+acs_status ranker_gradient(const float* feats, const float* times, int n, int F, int H, const float* params,
+                           float* grad, void* ws, size_t ws_bytes, cudaStream_t s) {
+    const Layout L(F, H);
+    if (ws_bytes < ranker_ws_bytes(n, F, H)) return fail(ACS_ERR_WORKSPACE, "ranker workspace too small");
+    // The target: the standardised log time, with the statistics stored in the model.
+    std::vector<float> ht(n), st(2);
+    if (cudaMemcpyAsync(ht.data(), times, n * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(st.data(), params + L.tmu, 2 * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return launch_status("ranker_gradient: reading times and target scale");
+    if (!(st[1] > 0.f)) return fail(ACS_ERR_NOMODEL, "model has no target scale");
+    std::vector<float> tstd(n);
+    for (int i = 0; i < n; ++i) {
+        if (!(ht[i] > 0.f)) return fail(ACS_ERR_INVALID, "time %d is not positive", i);
+        tstd[i] = (float)((std::log(ht[i]) - st[0]) / st[1]);
+    }
+    Ws w = carve(static_cast<float*>(ws), n, H, L.P);
+    if (cudaMemcpyAsync(w.T, tstd.data(), n * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return launch_status("ranker_gradient: uploading targets");
+    const int tb = H < 32 ? 32 : ((H + 31) / 32) * 32;
+    float* prm = const_cast<float*>(params);   // read only when grad is set
+    mlp_forward<<<n, tb, sizeof(float) * (F + 2 * H), s>>>(feats, params, F, H, w.H1, w.H2, w.Y, 1);
+    mlp_backward_sample<<<n, tb, sizeof(float) * H, s>>>(w.T, params, F, H, n, w.H1, w.H2, w.Y, w.DH1, w.DH2, w.DY);
+    mlp_grad_adam<<<(unsigned)((L.P + 255) / 256), 256, 0, s>>>(feats, w.H1, w.H2, w.DH1, w.DH2, w.DY, prm, w.m, w.v,
+                                                                 F, H, n, 1, 0.f, grad);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return launch_status("ranker_gradient kernels");
+    return launch_status("ranker_gradient kernels");
+}
+
+// Model file: "acs-ranker-model 1", then "F H P", then the P parameters one per line in
+// hexadecimal floating point (%a), so that a load gives back the same bits.
+acs_status ranker_save(const char* path, const float* params, int F, int H) {
+    const Layout L(F, H);
+    std::vector<float> p(L.P);
+    if (cudaMemcpy(p.data(), params, L.P * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return launch_status("ranker_save: reading the model");
+    FILE* f = fopen(path, "w");
+    if (!f) return fail(ACS_ERR_INVALID, "cannot open %s for writing", path);
+    bool ok = fprintf(f, "acs-ranker-model 1\n%d %d %zu\n", F, H, L.P) > 0;
+    for (size_t q = 0; q < L.P && ok; ++q) ok = fprintf(f, "%a\n", (double)p[q]) > 0;
+    ok = (fclose(f) == 0) && ok;
+    return ok ? ACS_OK : fail(ACS_ERR_INVALID, "writing %s failed", path);
+}
+
+acs_status ranker_load(const char* path, float* params, size_t capacity, int* F_out, int* H_out) {
+    FILE* f = fopen(path, "r");
+    if (!f) return fail(ACS_ERR_INVALID, "cannot open %s", path);
+    int ver = 0, F = 0, H = 0;
+    size_t P = 0;
+    char magic[32] = {0};
+    if (fscanf(f, "%31s %d", magic, &ver) != 2 || std::string(magic) != "acs-ranker-model" || ver != 1 ||
+        fscanf(f, "%d %d %zu", &F, &H, &P) != 3 || F < 1 || F > 1024 || H < 1 || H > 1024 ||
+        P != Layout(F, H).P) {
+        fclose(f);
+        return fail(ACS_ERR_INVALID, "%s is not an acs-ranker-model 1 file", path);
+    }
+    std::vector<float> p(P);
+    for (size_t q = 0; q < P; ++q) {
+        double v;
+        if (fscanf(f, "%la", &v) != 1 || !std::isfinite(v)) {
+            fclose(f);
+            return fail(ACS_ERR_INVALID, "%s: parameter %zu is missing or not finite", path, q);
+        }
+        p[q] = (float)v;
+    }
+    fclose(f);
+    if (F_out) *F_out = F;
+    if (H_out) *H_out = H;
+    if (!params) return ACS_OK;   // size query
+    if (capacity < P) return fail(ACS_ERR_WORKSPACE, "model needs %zu floats, buffer holds %zu", P, capacity);
+    if (cudaMemcpy(params, p.data(), P * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+        return launch_status("ranker_load: uploading the model");
+    return ACS_OK;
 }
 
 acs_status ranker_predict(const float* feats, int n, int F, int H, const float* params, float* scores, cudaStream_t s) {

@@ -29,148 +29,10 @@
 #include <vector>
 
 #include "acs_internal.cuh"
+#include "egraph.h"
 
 namespace acs {
 namespace rw {
-
-enum Op : int { CONST = 0, PARAM, LOAD, ADD, SUB, MUL, DIV, FMA, NEG, RCP, NOPS };
-static const char* kOpName[NOPS] = {"const", "param", "load", "add", "sub", "mul", "div", "fma", "neg", "rcp"};
-static int arity(int op) {
-    switch (op) {
-        case CONST: case PARAM: case LOAD: return 0;
-        case NEG: case RCP: return 1;
-        case FMA: return 3;
-        default: return 2;
-    }
-}
-
-// Parameters of the generated kernel (q[] array).
-enum Param : int { P_GAMMA = 0, P_EPS = 1, P_HX = 2, P_HY = 3, P_HZ = 4, P_ONE = 5, P_MONE = 6, P_NZ = 7 };
-
-struct Node {
-    int op;
-    int a, b, c;        // child e-classes (canonical after rebuild)
-    int64_t payload;    // CONST: double bits; PARAM: index; LOAD: comp * 13 + point
-};
-
-// Counter-based random stream (SplitMix64 mixing of seed + (counter+1) * golden ratio).
-struct Rng {
-    uint64_t seed, ctr = 0;
-    explicit Rng(uint64_t s) : seed(s) {}
-    uint64_t next() {
-        uint64_t z = seed + (++ctr) * 0x9E3779B97F4A7C15ULL;
-        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
-        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
-        return z ^ (z >> 31);
-    }
-    double uniform() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }
-    int below(int n) { return (int)(next() % (uint64_t)n); }
-};
-
-struct Key {
-    int op, a, b, c;
-    int64_t payload;
-    bool operator==(const Key& o) const { return op == o.op && a == o.a && b == o.b && c == o.c && payload == o.payload; }
-};
-struct KeyHash {
-    size_t operator()(const Key& k) const {
-        uint64_t h = (uint64_t)k.op * 0x9E3779B97F4A7C15ULL;
-        h ^= (uint64_t)(uint32_t)k.a + 0x85EBCA6B + (h << 6) + (h >> 2);
-        h ^= (uint64_t)(uint32_t)k.b + 0xC2B2AE35 + (h << 6) + (h >> 2);
-        h ^= (uint64_t)(uint32_t)k.c + 0x27D4EB2F + (h << 6) + (h >> 2);
-        h ^= (uint64_t)k.payload + 0x165667B1 + (h << 6) + (h >> 2);
-        return (size_t)h;
-    }
-};
-
-class EGraph {
-   public:
-    std::vector<Node> nodes;
-    std::vector<int> node_class;  // class id (not necessarily canonical) of each node
-    std::vector<int> parent;      // union-find over class ids
-    std::unordered_map<Key, int, KeyHash> memo;
-    int nclasses = 0;
-
-    int find(int x) {
-        while (parent[x] != x) {
-            parent[x] = parent[parent[x]];
-            x = parent[x];
-        }
-        return x;
-    }
-    Key key_of(const Node& n) {
-        const int ar = arity(n.op);
-        return Key{n.op, ar > 0 ? find(n.a) : -1, ar > 1 ? find(n.b) : -1, ar > 2 ? find(n.c) : -1, n.payload};
-    }
-    int add(int op, int a = -1, int b = -1, int c = -1, int64_t payload = 0) {
-        Node n{op, a, b, c, payload};
-        Key k = key_of(n);
-        auto it = memo.find(k);
-        if (it != memo.end()) return find(node_class[it->second]);
-        n.a = k.a;
-        n.b = k.b;
-        n.c = k.c;
-        nodes.push_back(n);
-        const int cls = nclasses++;
-        parent.push_back(cls);
-        node_class.push_back(cls);
-        memo.emplace(k, (int)nodes.size() - 1);
-        return cls;
-    }
-    int cnst(double v) {
-        int64_t bits;
-        std::memcpy(&bits, &v, 8);
-        return add(CONST, -1, -1, -1, bits);
-    }
-    bool merge(int x, int y) {
-        x = find(x);
-        y = find(y);
-        if (x == y) return false;
-        if (x > y) std::swap(x, y);
-        parent[y] = x;
-        return true;
-    }
-    // Restore the congruence invariant: nodes with equal canonical keys share a class.
-    void rebuild() {
-        for (int pass = 0; pass < 64; ++pass) {
-            std::unordered_map<Key, int, KeyHash> m;
-            m.reserve(nodes.size() * 2);
-            bool changed = false;
-            for (size_t i = 0; i < nodes.size(); ++i) {
-                Key k = key_of(nodes[i]);
-                auto it = m.find(k);
-                if (it == m.end())
-                    m.emplace(k, (int)i);
-                else if (merge(node_class[it->second], node_class[i]))
-                    changed = true;
-            }
-            if (!changed) {
-                memo.swap(m);
-                for (auto& n : nodes) {
-                    const int ar = arity(n.op);
-                    if (ar > 0) n.a = find(n.a);
-                    if (ar > 1) n.b = find(n.b);
-                    if (ar > 2) n.c = find(n.c);
-                }
-                return;
-            }
-        }
-    }
-    // nodes of each canonical class
-    std::vector<std::vector<int>> class_nodes() {
-        std::vector<std::vector<int>> cn(nclasses);
-        for (size_t i = 0; i < nodes.size(); ++i) cn[find(node_class[i])].push_back((int)i);
-        return cn;
-    }
-    bool const_value(const std::vector<std::vector<int>>& cn, int cls, double* v) {
-        for (int ni : cn[find(cls)])
-            if (nodes[ni].op == CONST) {
-                std::memcpy(v, &nodes[ni].payload, 8);
-                return true;
-            }
-        return false;
-    }
-};
 
 // ------------------------------------------------------------------ the as-written body
 
@@ -217,227 +79,6 @@ Body build_as_written(EGraph& g) {
         b.root[s] = g.add(SUB, g.add(NEG, fl), g.add(MUL, eps, diss));
     }
     return b;
-}
-
-// ------------------------------------------------------------------ rules
-
-enum Family : int { F_FMA = 0, F_COMM, F_ASSOC, F_FOLD, F_DIV, F_DISTRIB, F_SUBNEG, NFAM };
-
-// Exact constant folding only: the folded double must equal the exact result.
-static bool exact_add(double a, double b, double* r) {
-    const double s = a + b, bb = s - a, err = (a - (s - bb)) + (b - bb);
-    *r = s;
-    return err == 0.0 && std::isfinite(s);
-}
-static bool exact_mul(double a, double b, double* r) {
-    const double p = a * b;
-    *r = p;
-    return std::fma(a, b, -p) == 0.0 && std::isfinite(p);
-}
-
-struct Pending {
-    int cls;       // e-class the new expression joins
-    int op, a, b, c;
-    int64_t payload;
-    int inner_op = -1, ia = -1, ib = -1;  // optional child built first, placed in slot inner_slot
-    int inner_slot = -1;
-};
-
-class Rewriter {
-   public:
-    EGraph& g;
-    explicit Rewriter(EGraph& eg) : g(eg) {}
-
-    // Collect the matches of one family over all e-nodes.
-    void match(int fam, const std::vector<std::vector<int>>& cn, std::vector<Pending>& out, std::vector<int>& unions) {
-        auto has = [&](int cls, int op, std::vector<const Node*>& found) {
-            found.clear();
-            for (int ni : cn[g.find(cls)])
-                if (g.nodes[ni].op == op) found.push_back(&g.nodes[ni]);
-            return !found.empty();
-        };
-        std::vector<const Node*> f1, f2;
-        const size_t nn = g.nodes.size();
-        for (size_t i = 0; i < nn; ++i) {
-            const Node n = g.nodes[i];
-            const int cls = g.find(g.node_class[i]);
-            switch (fam) {
-                case F_FMA:
-                    if (n.op == ADD) {
-                        for (int side = 0; side < 2; ++side) {
-                            const int x = side ? n.a : n.b, other = side ? n.b : n.a;
-                            if (has(x, MUL, f1))
-                                for (auto* m : f1) out.push_back({cls, FMA, m->a, m->b, other, 0});
-                        }
-                    } else if (n.op == SUB) {
-                        if (has(n.b, MUL, f1))  // A - B*C -> FMA(-B, C, A)
-                            for (auto* m : f1) {
-                                Pending p{cls, FMA, -2, m->b, n.a, 0};
-                                p.inner_op = NEG, p.ia = m->a, p.inner_slot = 0;
-                                out.push_back(p);
-                            }
-                        if (has(n.a, MUL, f1))  // B*C - A -> FMA(B, C, -A)
-                            for (auto* m : f1) {
-                                Pending p{cls, FMA, m->a, m->b, -2, 0};
-                                p.inner_op = NEG, p.ia = n.b, p.inner_slot = 2;
-                                out.push_back(p);
-                            }
-                    }
-                    break;
-                case F_COMM:
-                    if (n.op == ADD || n.op == MUL) out.push_back({cls, n.op, n.b, n.a, -1, 0});
-                    break;
-                case F_ASSOC:
-                    if (n.op == ADD || n.op == MUL) {
-                        if (has(n.b, n.op, f1))  // A op (B op C) -> (A op B) op C
-                            for (auto* m : f1) {
-                                Pending p{cls, n.op, -2, m->b, -1, 0};
-                                p.inner_op = n.op, p.ia = n.a, p.ib = m->a, p.inner_slot = 0;
-                                out.push_back(p);
-                            }
-                        if (has(n.a, n.op, f1))  // (A op B) op C -> A op (B op C)
-                            for (auto* m : f1) {
-                                Pending p{cls, n.op, m->a, -2, -1, 0};
-                                p.inner_op = n.op, p.ia = m->b, p.ib = n.b, p.inner_slot = 1;
-                                out.push_back(p);
-                            }
-                    }
-                    break;
-                case F_FOLD: {
-                    double x, y, r;
-                    if ((n.op == ADD || n.op == SUB || n.op == MUL) && g.const_value(cn, n.a, &x) &&
-                        g.const_value(cn, n.b, &y)) {
-                        const bool ok = n.op == MUL ? exact_mul(x, y, &r) : exact_add(x, n.op == SUB ? -y : y, &r);
-                        if (ok) {
-                            int64_t bits;
-                            std::memcpy(&bits, &r, 8);
-                            out.push_back({cls, CONST, -1, -1, -1, bits});
-                        }
-                    } else if (n.op == NEG && g.const_value(cn, n.a, &x)) {
-                        r = -x;
-                        int64_t bits;
-                        std::memcpy(&bits, &r, 8);
-                        out.push_back({cls, CONST, -1, -1, -1, bits});
-                    } else if (n.op == ADD) {
-                        if (g.const_value(cn, n.b, &y) && y == 0.0 && !std::signbit(y)) unions.push_back(cls), unions.push_back(n.a);
-                        if (g.const_value(cn, n.a, &x) && x == 0.0 && !std::signbit(x)) unions.push_back(cls), unions.push_back(n.b);
-                    } else if (n.op == MUL) {
-                        if (g.const_value(cn, n.b, &y) && y == 1.0) unions.push_back(cls), unions.push_back(n.a);
-                        if (g.const_value(cn, n.a, &x) && x == 1.0) unions.push_back(cls), unions.push_back(n.b);
-                    }
-                    break;
-                }
-                case F_DIV:
-                    if (n.op == DIV) {  // A / B -> A * rcp(B)
-                        Pending p{cls, MUL, n.a, -2, -1, 0};
-                        p.inner_op = RCP, p.ia = n.b, p.inner_slot = 1;
-                        out.push_back(p);
-                        if (has(n.a, MUL, f1))  // (A*B)/C -> A * (B/C)
-                            for (auto* m : f1) {
-                                Pending q{cls, MUL, m->a, -2, -1, 0};
-                                q.inner_op = DIV, q.ia = m->b, q.ib = n.b, q.inner_slot = 1;
-                                out.push_back(q);
-                            }
-                    } else if (n.op == MUL && has(n.b, DIV, f1)) {  // A * (B/C) -> (A*B)/C
-                        for (auto* m : f1) {
-                            Pending q{cls, DIV, -2, m->b, -1, 0};
-                            q.inner_op = MUL, q.ia = n.a, q.ib = m->a, q.inner_slot = 0;
-                            out.push_back(q);
-                        }
-                    }
-                    break;
-                case F_DISTRIB:
-                    if ((n.op == ADD || n.op == SUB) && has(n.a, MUL, f1) && has(n.b, MUL, f2)) {
-                        // A*B +- A*C -> A * (B +- C)  (common left factor, same e-class)
-                        for (auto* m1 : f1)
-                            for (auto* m2 : f2) {
-                                if (g.find(m1->a) == g.find(m2->a)) {
-                                    Pending p{cls, MUL, m1->a, -2, -1, 0};
-                                    p.inner_op = n.op, p.ia = m1->b, p.ib = m2->b, p.inner_slot = 1;
-                                    out.push_back(p);
-                                }
-                                if (g.find(m1->b) == g.find(m2->b)) {
-                                    Pending p{cls, MUL, -2, m1->b, -1, 0};
-                                    p.inner_op = n.op, p.ia = m1->a, p.ib = m2->a, p.inner_slot = 0;
-                                    out.push_back(p);
-                                }
-                            }
-                    }
-                    break;
-                case F_SUBNEG:
-                    if (n.op == SUB) {  // A - B -> A + (-B)
-                        Pending p{cls, ADD, n.a, -2, -1, 0};
-                        p.inner_op = NEG, p.ia = n.b, p.inner_slot = 1;
-                        out.push_back(p);
-                    } else if (n.op == ADD && has(n.b, NEG, f1)) {  // A + (-B) -> A - B
-                        for (auto* m : f1) out.push_back({cls, SUB, n.a, m->a, -1, 0});
-                    } else if (n.op == NEG && has(n.a, NEG, f1)) {  // -(-A) -> A
-                        for (auto* m : f1) unions.push_back(cls), unions.push_back(m->a);
-                    }
-                    break;
-            }
-        }
-    }
-
-    // Apply matches; returns the number of new nodes or merges.
-    int apply(std::vector<Pending>& ps, std::vector<int>& unions, size_t node_limit) {
-        int changes = 0;
-        for (auto& p : ps) {
-            if (g.nodes.size() >= node_limit) break;
-            int args[3] = {p.a, p.b, p.c};
-            if (p.inner_slot >= 0) {
-                int inner;
-                if (p.inner_op == NEG || p.inner_op == RCP)
-                    inner = g.add(p.inner_op, p.ia);
-                else
-                    inner = g.add(p.inner_op, p.ia, p.ib);
-                args[p.inner_slot] = inner;
-            }
-            const size_t before = g.nodes.size();
-            const int nc = g.add(p.op, args[0], args[1], args[2], p.payload);
-            if (g.merge(nc, p.cls) || g.nodes.size() != before) ++changes;
-        }
-        for (size_t i = 0; i + 1 < unions.size(); i += 2)
-            if (g.merge(unions[i], unions[i + 1])) ++changes;
-        return changes;
-    }
-};
-
-// ------------------------------------------------------------------ extraction
-
-struct Extracted {
-    std::vector<int> best;  // best node per canonical class (-1 if none)
-};
-
-static const double kPaperCost[NOPS] = {0.0, 1.0, 100.0, 10.0, 10.0, 10.0, 100.0, 10.0, 10.0, 100.0};
-
-Extracted extract(EGraph& g, const double* opcost) {
-    auto cn = g.class_nodes();
-    const int nc = g.nclasses;
-    std::vector<double> cost(nc, INFINITY);
-    Extracted ex;
-    ex.best.assign(nc, -1);
-    for (int pass = 0; pass < 200; ++pass) {
-        bool changed = false;
-        for (int c = 0; c < nc; ++c) {
-            if (g.find(c) != c) continue;
-            for (int ni : cn[c]) {
-                const Node& n = g.nodes[ni];
-                double s = opcost[n.op];
-                const int ar = arity(n.op);
-                if (ar > 0) s += cost[g.find(n.a)];
-                if (ar > 1) s += cost[g.find(n.b)];
-                if (ar > 2) s += cost[g.find(n.c)];
-                if (s < cost[c] - 1e-9) {
-                    cost[c] = s;
-                    ex.best[c] = ni;
-                    changed = true;
-                }
-            }
-        }
-        if (!changed) break;
-    }
-    return ex;
 }
 
 // ------------------------------------------------------------------ codegen + features
@@ -678,28 +319,15 @@ acs_status variant_generate(unsigned long long seed, int index, char* src, size_
     if (index > 0) {
         // variant-specific rule families, order, limits and cost perturbation
         std::vector<int> fams;
-        for (int f = 0; f < NFAM; ++f) {
+        for (int f = 0; f < NFAM_PAPER; ++f) {
             const double pon = (f == F_FMA || f == F_FOLD) ? 0.8 : 0.55;
             if (rng.uniform() < pon) fams.push_back(f);
         }
         for (int k = (int)fams.size() - 1; k > 0; --k) std::swap(fams[k], fams[rng.below(k + 1)]);
         const int max_iters = 1 + rng.below(10);
         const size_t node_limit = 2000 + (size_t)rng.below(8001);
-        Rewriter rw(g);
-        for (iters = 0; iters < max_iters && g.nodes.size() < node_limit; ++iters) {
-            int changes = 0;
-            for (int f : fams) {
-                auto cn = g.class_nodes();
-                std::vector<Pending> ps;
-                std::vector<int> unions;
-                rw.match(f, cn, ps, unions);
-                changes += rw.apply(ps, unions, node_limit);
-                g.rebuild();
-                if (g.nodes.size() >= node_limit) break;
-            }
-            if (changes == 0) break;
-        }
-        for (int k = CONST + 1; k < NOPS; ++k) opcost[k] *= 0.6 + 0.8 * rng.uniform();
+        iters = saturate(g, fams, max_iters, node_limit);
+        for (int k = CONST + 1; k <= RCP; ++k) opcost[k] *= 0.6 + 0.8 * rng.uniform();
         bulk = rng.uniform() < 0.5;
         pipe = rng.uniform() < 0.5;
         static const int bxs[3] = {32, 64, 128};

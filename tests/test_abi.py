@@ -208,3 +208,36 @@ def test_block_form_rejects_bad_arguments(lib):
     huge = binding.Grid(nx, ny, nz, 1, X, X * X, X ** 3, nx, nx * ny, 1 << 58)
     assert lib.acs_block_form(A, B, G, OUT, ctypes.byref(huge), prm, f, None) == 1
     assert lib.acs_block_form(A, B, G, A + 8 * 100, ctypes.byref(g), prm, f, None) == 7   # overlaps A
+
+
+def test_probe_and_selftest_entry_points_reject_bad_arguments(lib):
+    ops = ctypes.c_longlong(-1)
+    assert lib.acs_fp64_rate_probe(None, 4, 256, 10, ctypes.byref(ops), None) == 1
+    for blocks, threads, iters in ((0, 256, 10), (4, 48, 10), (4, 2048, 10), (4, 256, 0)):
+        assert lib.acs_fp64_rate_probe(FAKE_U, blocks, threads, iters, None, None) == 1
+    assert lib.acs_fp64_rate_probe(FAKE_U + 4, 4, 256, 10, None, None) == 2
+    assert lib.acs_rcp_selftest(FAKE_U, FAKE_R, -1, None) == 1
+    assert lib.acs_rcp_selftest(None, FAKE_R, 8, None) == 1
+    assert lib.acs_rcp_selftest(FAKE_U, FAKE_U + 8, 8, None) == 7        # y overlaps x
+    assert lib.acs_rcp_selftest(FAKE_U, FAKE_R, 0, None) == 0            # nothing to do
+
+
+def test_ranker_gradient_and_model_files_reject_bad_arguments(lib, tmp_path):
+    assert lib.acs_ranker_gradient(None, FAKE_R, 8, 4, 16, FAKE_U, FAKE_R, FAKE_U, 1 << 20, None) == 1
+    assert lib.acs_ranker_gradient(FAKE_U, FAKE_R, 0, 4, 16, FAKE_U, FAKE_R, FAKE_U, 1 << 20, None) == 1
+    assert lib.acs_ranker_save(None, None) == 1
+    bad = tmp_path / "bad.model"
+    bad.write_text("acs-ranker-model 1\n3 4 999\n")
+    F, H = ctypes.c_int(), ctypes.c_int()
+    assert lib.acs_ranker_load(str(bad).encode(), None, 0, ctypes.byref(F), ctypes.byref(H)) == 1
+    bad.write_text("not a model\n")
+    assert lib.acs_ranker_load(str(bad).encode(), None, 0, None, None) == 1
+    assert lib.acs_ranker_load(str(tmp_path / "missing").encode(), None, 0, None, None) == 1
+    # a well-formed file is read for its sizes without touching a device (params NULL)
+    n_par = binding.acs_ranker_param_count(3, 4)
+    good = tmp_path / "good.model"
+    good.write_text("acs-ranker-model 1\n3 4 %d\n" % n_par + "0x1p-2\n" * n_par)
+    assert lib.acs_ranker_load(str(good).encode(), None, 0, ctypes.byref(F), ctypes.byref(H)) == 0
+    assert (F.value, H.value) == (3, 4)
+    good.write_text("acs-ranker-model 1\n3 4 %d\n" % n_par + "0x1p-2\n" * (n_par - 1) + "nan\n")
+    assert lib.acs_ranker_load(str(good).encode(), None, 0, None, None) == 1

@@ -42,5 +42,10 @@ def test_default_arm_line():
     r = d["roofline"]
     assert r["bound"] == "alu" and 0 < r["frac"] <= 1.05 and r["achieved"] == pytest.approx(r["frac"] * r["peak"])
     assert d["gpu_launches"] == 5
+    # the roofline's peak is the FP64 probe measured in the run; the derived peak sits beside it
+    assert r["peak"] == pytest.approx(d["fp64_probe"]["gops"]) and r["peak_derived"] > 0
+    assert 1.5 < d["fp64_probe"]["op_per_clk_per_sm"] <= 2.05
+    # in-process clock samples over the timed legs
+    assert d["clocks"]["samples"] >= 10 and d["clocks"]["sm_mhz"] > 0
     e = d["e2e"]
     assert e["value"] > 0 and e["h2d_bytes_per_step"] == 703040000 and e["d2h_bytes_per_step"] == 671088640
