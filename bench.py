@@ -466,56 +466,54 @@ def bench_batch(torch, binding, inputs, stream, steps: int) -> dict:
     return res
 
 
-def run_large(args) -> None:
-    """RHS 512^3 (as written, ACCSAT, ranker-picked variant, autotuned saturated) and the star
-    stencil at 768^3 (as written, autotuned saturated); one JSON line with fractions of the
-    FP64-pipe and HBM rooflines."""
-    import torch
-    from paper_2306_13002_gb300 import binding, inputs, ranker
-    from paper_2306_13002_gb300 import build as acs_build
-    acs_build.build()
-    stream = torch.cuda.current_stream()
-    steps = max(3, min(args.steps, 10))
-    peaks = measured_peaks()
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    sms = int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
-    peak = fp64_probe(torch, binding, stream, sms, None)["gops"]
-    out = {"study": "large workloads", "unit": UNIT, "fp64_peak_measured_gops": peak}
-    # ranker-picked variant: a 128-variant study at 256^3, then the pick is timed at 512^3
-    small = ranker.study(n_variants=128, n_train=100, n=256, epochs=2000, reps=3)
+def bench_ranker(binding, ranker, n_variants: int = 512) -> dict:
+    """The learned ranker on the saturated (march-scope) variants at 256^3: a study of the distinct
+    ones among `n_variants` rewriter variants (78 % train, the rest ranked by the MLP and by the
+    paper's analytical cost), every variant checked against the library's saturated kernel."""
+    t = time.time()
+    res = ranker.study(n_variants=n_variants, n=N_RHS, epochs=2000, reps=3, scope=binding.SCOPE_MARCH)
+    res["wall_s"] = time.time() - t
+    return res
+
+
+def bench_large(torch, binding, inputs, stream, peak_gops: float, pick_index: int | None, steps: int) -> dict:
+    """RHS 512^3 (as written, autotuned saturated, the ranker-picked saturated variant) and the star
+    stencil at 768^3 (as written, autotuned saturated), with fractions of the FP64-pipe roofline
+    (measured peak) and of HBM."""
+    from paper_2306_13002_gb300 import ranker  # noqa: F401
+    hbm = float(measured_peaks().get("hbm_gbs", 6800.0))
+    out = {"fp64_peak_gops": peak_gops}
     n = 512
     U = torch.from_numpy(inputs.rhs_field(n, halo=2, seed=inputs.SEED_HUGE)).cuda()
     R = torch.empty((5, n, n, n), dtype=torch.float64, device="cuda")
     pts = n ** 3
     algo_bytes = (U.numel() + R.numel()) * 8
     rhs = {"grid": [n] * 3, "in_gb": U.numel() * 8 / 1e9, "out_gb": R.numel() * 8 / 1e9}
-    tile, _ = binding.acs_autotune_rhs(U, R)
-    for form, fn in (("as_written", lambda: binding.acs_rhs_form(U, R, "as_written")),
-                     ("accsat", lambda: binding.acs_rhs_form(U, R, "accsat")),
-                     ("saturated_autotuned", lambda: binding.acs_rhs_saturated(U, R, tile=tile))):
+    tile, _ = binding.acs_autotune_rhs(U, R, stream=stream)
+    forms = [("as_written", lambda: binding.acs_rhs_plain(U, R, stream=stream)),
+             ("saturated_autotuned", lambda: binding.acs_rhs_saturated(U, R, tile=tile, stream=stream))]
+    pick = None
+    if pick_index is not None:
+        src, _, info = binding.acs_variant_generate(inputs.SEED_VARIANTS, pick_index, binding.SCOPE_MARCH)
+        pick = binding.Variant(src, info)
+        forms.append(("ranker_pick_variant", lambda: binding.acs_rhs_saturated(U, R, variant=pick, stream=stream)))
+    for form, fn in forms:
         fn()
         torch.cuda.synchronize()
         _, rm = time_launches(torch, fn, steps, stream)
         ms = rm / steps
         rhs[form] = {"ms": ms, "gpts": pts / (ms * 1e-3) / 1e9}
-    # the variants the learned ranker and the analytical cost picked at 256^3, timed at 512^3
-    for name, key in (("mlp_pick_variant", "mlp_pick_index"), ("analytical_pick_variant", "analytical_pick_index")):
-        src, _, info = binding.acs_variant_generate(inputs.SEED_VARIANTS, small[key])
-        m = binding.Variant(src, info.block_x)
-        fn = lambda: m.launch(U, R)  # noqa: E731
-        fn()
-        torch.cuda.synchronize()
-        _, rm = time_launches(torch, fn, steps, stream)
-        rhs[name] = {"ms": rm / steps, "gpts": pts / (rm / steps * 1e-3) / 1e9, "index": small[key]}
-        m.close()
+    if pick is not None:
+        rhs["ranker_pick_variant"].update({"index": pick_index, "shape": [*pick.block, pick.flags],
+                                           "fp64_frac_at_116_ops": DP_OPS_PER_POINT["rhs_saturated"] * pts /
+                                           (rhs["ranker_pick_variant"]["ms"] * 1e-3) / 1e9 / peak_gops})
+        pick.close()
     sat = rhs["saturated_autotuned"]["ms"]
     rhs["tile"] = list(tile)
-    rhs["fp64_frac"] = DP_OPS_PER_POINT["rhs_saturated"] * pts / (sat * 1e-3) / 1e9 / peak
+    rhs["fp64_frac"] = DP_OPS_PER_POINT["rhs_saturated"] * pts / (sat * 1e-3) / 1e9 / peak_gops
     rhs["hbm_frac"] = algo_bytes / (sat * 1e-3) / 1e9 / hbm
     rhs["speedup_saturated_over_as_written"] = rhs["as_written"]["ms"] / sat
     out["rhs_512"] = rhs
-    out["ranker_study_256"] = {k: small[k] for k in ("spearman_mlp_test", "spearman_analytical_test",
-                                                    "mlp_pick_over_best", "analytical_pick_over_best")}
     del U, R
     torch.cuda.empty_cache()
     n = 768
@@ -526,9 +524,9 @@ def run_large(args) -> None:
     pts = n ** 3
     algo_bytes = (u.numel() + a.numel() + o.numel()) * 8
     st = {"grid": [n] * 3}
-    tile, _ = binding.acs_autotune_stencil(u, a, o)
-    for form, fn in (("as_written", lambda: binding.acs_stencil_plain(u, a, o)),
-                     ("saturated_autotuned", lambda: binding.acs_stencil_saturated(u, a, o, tile=tile))):
+    tile, _ = binding.acs_autotune_stencil(u, a, o, stream=stream)
+    for form, fn in (("as_written", lambda: binding.acs_stencil_plain(u, a, o, stream=stream)),
+                     ("saturated_autotuned", lambda: binding.acs_stencil_saturated(u, a, o, tile=tile, stream=stream))):
         fn()
         torch.cuda.synchronize()
         _, rm = time_launches(torch, fn, steps, stream)
@@ -536,11 +534,27 @@ def run_large(args) -> None:
         st[form] = {"ms": ms, "gpts": pts / (ms * 1e-3) / 1e9}
     sat = st["saturated_autotuned"]["ms"]
     st["tile"] = list(tile)
-    st["fp64_frac"] = DP_OPS_PER_POINT["star_saturated"] * pts / (sat * 1e-3) / 1e9 / peak
+    st["fp64_frac"] = DP_OPS_PER_POINT["star_saturated"] * pts / (sat * 1e-3) / 1e9 / peak_gops
     st["hbm_frac"] = algo_bytes / (sat * 1e-3) / 1e9 / hbm
     st["speedup_saturated_over_as_written"] = st["as_written"]["ms"] / sat
     out["stencil_768"] = st
-    print(json.dumps(out))
+    del u, a, o
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_large(args) -> None:
+    """--large alone: the ranker study (512 variants at 256^3), then the large workloads."""
+    import torch
+    from paper_2306_13002_gb300 import binding, inputs, ranker
+    from paper_2306_13002_gb300 import build as acs_build
+    acs_build.build()
+    stream = torch.cuda.current_stream()
+    sms = int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+    peak = fp64_probe(torch, binding, stream, sms, None)["gops"]
+    study = bench_ranker(binding, ranker)
+    res = bench_large(torch, binding, inputs, stream, peak, study["mlp_pick_index"], max(3, min(args.steps, 10)))
+    print(json.dumps({"study": "large workloads", "unit": UNIT, "ranker_256": study, **res}))
 
 
 def main() -> None:
@@ -553,10 +567,14 @@ def main() -> None:
     ap.add_argument("--no-stencil", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the as-written timing")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end timing")
+    ap.add_argument("--no-ranker", action="store_true", help="skip the learned-ranker study (and the large block)")
+    ap.add_argument("--no-large", action="store_true", help="skip RHS 512^3 and the star stencil at 768^3")
     ap.add_argument("--n", type=int, default=N_RHS, help="RHS interior side (256 is the benchmark workload)")
     ap.add_argument("--ranker", action="store_true",
                     help="instead of the step benchmark: the rewriter-variant ranker study (512 variants at 256^3)")
     ap.add_argument("--variants", type=int, default=512)
+    ap.add_argument("--scope", default="march", choices=["march", "iteration"],
+                    help="--ranker: rank cross-iteration saturated kernels (march) or per-point bodies")
     ap.add_argument("--tile", default="", help="bx,by,kchunk[,flags]: use this launch shape instead of the autotuner")
     ap.add_argument("--large", action="store_true",
                     help="instead of the step benchmark: RHS 512^3 and star stencil 768^3, all forms")
@@ -587,11 +605,12 @@ def main() -> None:
         print(json.dumps({"workload": "star_stencil_batch_64_grids_fp64", "unit": "ms per batch", **res}))
         return
     if args.ranker:
+        from paper_2306_13002_gb300 import binding, ranker
         from paper_2306_13002_gb300 import build as acs_build
-        from paper_2306_13002_gb300 import ranker
         acs_build.build()
         t = time.time()
-        res = ranker.study(n_variants=args.variants, n_train=int(round(args.variants * 400 / 512)), n=args.n)
+        res = ranker.study(n_variants=args.variants, n=args.n,
+                           scope=binding.SCOPE_ITERATION if args.scope == "iteration" else binding.SCOPE_MARCH)
         res["wall_s"] = time.time() - t
         print(json.dumps({"study": "learned variant ranker", "metric": "chosen-variant time / measured best",
                           "unit": "ratio", **res}))
@@ -828,6 +847,21 @@ def run_ours(args) -> None:
     }
     if not args.no_stencil:
         result["block_128"] = bench_block(torch, binding, inputs, stream, max(3, min(args.steps, 20)))
+    if not args.no_ranker:
+        from paper_2306_13002_gb300 import ranker
+        torch.cuda.empty_cache()
+        study = bench_ranker(binding, ranker)
+        keys = ("variants_generated", "variants_distinct", "train", "test", "spearman_mlp_test",
+                "spearman_analytical_test", "best_test_ms", "mlp_pick_ms", "analytical_pick_ms", "mlp_pick_over_best",
+                "analytical_pick_over_best", "all_ms_min", "all_ms_median", "all_ms_max",
+                "max_err_over_tol_vs_saturated", "mlp_pick_index", "mlp_pick_shape", "best_all_index", "wall_s")
+        result["ranker"] = {"workload": f"march-scope rewriter variants of the RHS at {N_RHS}^3",
+                            **{k: study[k] for k in keys},
+                            "builtin_saturated_ms": ms_per_step,
+                            "mlp_pick_over_builtin": study["mlp_pick_ms"] / ms_per_step}
+        if not args.no_large:
+            result["large"] = bench_large(torch, binding, inputs, stream, peak, study["mlp_pick_index"],
+                                          max(3, min(args.steps, 10)))
     if not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(U_host)
     print(json.dumps(result))

@@ -106,6 +106,9 @@ typedef enum acs_form {
     ACS_FORM_SATURATED = 5
 } acs_form;
 
+/* A compiled rewriter variant (acs_variant_build); opaque. */
+typedef struct acs_variant_module *acs_variant_handle;
+
 /* Launch shape of a saturated kernel. A NULL tile selects the built-in default (or the shape
  * the autotuner recorded for the grid size). */
 typedef struct acs_tile {
@@ -147,12 +150,19 @@ acs_status acs_rhs_plain(const double *U, double *R, const acs_grid *g, const ac
  * the six neighbours, one reciprocal per point, dissipation reassociated as
  * sum(U at +-2) - 4 sum(U at +-1) + 18 U, FMA throughout, and every plane of U staged in
  * shared memory ahead of the arithmetic (bulk load). Same arguments as acs_rhs_plain plus
- *   tile   launch shape or NULL (the autotuned shape for this grid size if acs_autotune_rhs
- *          recorded one, else 16 x 16 with the balanced schedule and TMA plane staging where
- *          the layout allows it).
+ *   tile     launch shape or NULL (the autotuned shape for this grid size if acs_autotune_rhs
+ *            recorded one, else 16 x 16 with the balanced schedule and TMA plane staging where
+ *            the layout allows it).
+ *   variant  NULL for the library's own saturated kernel, or a march-scope rewriter variant
+ *            (acs_variant_generate with ACS_SCOPE_MARCH, acs_variant_build), for instance the
+ *            one the learned ranker put first (acs_variant_rank). A variant is compiled for its
+ *            block shape, staging and schedule: `tile` must then be NULL or carry the
+ *            variant's bx, by and flags (only kchunk is free, for the z-chunk schedule).
+ *            ACS_ERR_INVALID for an iteration-scope variant or a mismatched tile;
+ *            ACS_ERR_UNSUPPORTED for a TMA-staged variant on a layout TMA cannot copy.
  */
 acs_status acs_rhs_saturated(const double *U, double *R, const acs_grid *g, const acs_rhs_params *p,
-                             const acs_tile *tile, acs_stream stream);
+                             const acs_tile *tile, acs_variant_handle variant, acs_stream stream);
 
 /*
  * acs_rhs_saturated_host - the saturated RHS on HOST arrays, streamed through the GPU in
@@ -297,38 +307,69 @@ int acs_tune_cache_size(void);
 /* ---------------------------------------------------------------------------------------
  * Host rewriter of the RHS body (paper Sec. IV-VI) and its learned ranker.
  *
- * acs_variant_generate builds the as-written body in an e-graph, saturates it with the
- * Table I rules plus the rule families the paper leaves off (division, distributivity,
- * subtraction/negation), drawing the families, their order and the limits (at most 10,000
- * e-nodes, 10 iterations) from (seed, index), extracts one program under the paper's cost
- * model (Sec. V-B) with per-variant cost factors, and emits it as a CUDA kernel (first-use
- * or bulk-load order, Sec. VI). index 0 is the body with only hash-consing (plain CSE).
+ * acs_variant_generate builds a body in an e-graph, saturates it with the Table I rules plus
+ * the rule families the paper leaves off (division, distributivity, subtraction/negation) and,
+ * in the march scope, like-term collection, drawing the families, their order and the limits
+ * (at most 10,000 e-nodes, 10 iterations) from (seed, index), extracts one program under the
+ * paper's cost model (Sec. V-B) with per-variant cost factors, and emits it as a CUDA kernel.
+ * Two scopes:
+ *   ACS_SCOPE_ITERATION  the paper's scope (Sec. IV-A): the as-written loop body of one point,
+ *                        rewritten on its own, one thread per point (first-use or bulk-load
+ *                        order, Sec. VI); index 0 is the body with only hash-consing (CSE).
+ *   ACS_SCOPE_MARCH      across neighbouring iterations: the body split at the flux of a point
+ *                        (the subexpression every statement differencing that point shares)
+ *                        into a flux program, evaluated once per point, and a combine program
+ *                        per component, each saturated and extracted on its own e-graph and
+ *                        emitted into the saturated march kernel (x/y fluxes shared through
+ *                        shared memory, z fluxes through registers, planes staged ahead). A
+ *                        variant also draws its instruction lowering, tile, plane staging and
+ *                        schedule (info->block_x, block_y, flags). index 0: hash-consing only,
+ *                        16 x 16, balanced, TMA.
  * Host only; no GPU is touched. `src` / `dag` may be NULL; a too-small buffer returns
  * ACS_ERR_INVALID with the needed size in info->src_bytes / dag_bytes.
  * The DAG text has one line "id op a b c payload" per extracted node in emission order
- * (op in const, param, load, add, sub, mul, div, fma, neg, rcp; fma(a,b,c) = a*b + c;
+ * (op in const, param, load, add, sub, mul, div, fma, neg, rcp, flux; fma(a,b,c) = a*b + c;
  * const payload = IEEE bits; load payload = component * 13 + point, points 0 = p,
  * 1..6 = +x,-x,+y,-y,+z,-z, 7..12 = the same at distance 2; param 0 gamma, 1 eps,
- * 2..4 = 1/(2h)) and a line "R c id" per output component.
+ * 2..4 = 1/(2h)) and a line "R c id" per output component. In the march scope the text has
+ * two sections: "flux" (loads of point 0 only) ending with lines "F d s id" (F_d,s, d = 0..2
+ * for x, y, z, s = 1..4), then "combine", whose flux nodes are the neighbour fluxes (payload
+ * d * 8 + (s - 1) * 2 + side, side 0 = p + e_d, 1 = p - e_d), ending with the "R c id" lines.
  * ------------------------------------------------------------------------------------- */
-#define ACS_VARIANT_NFEAT 16
+#define ACS_VARIANT_NFEAT 20
+typedef enum acs_scope {
+    ACS_SCOPE_ITERATION = 0,
+    ACS_SCOPE_MARCH = 1
+} acs_scope;
+/* Static features (names from acs_variant_feature_name), per interior point:
+ *  0 paper_cost  1 n_add (add + sub)  2 n_mul  3 n_fma  4 n_div (IEEE divisions and reciprocals)
+ *  5 n_neg  6 n_load (march: combine reads + 5)  7 n_load_x (march: combine loads)
+ *  8 n_load_yz (march: neighbour-flux reads)  9 n_nodes  10 max_live  11 bulk  12 pipe
+ *  13 block_x  14 regs (filled by the caller after acs_variant_build)  15 dp_ops_est
+ *  16 block_y  17 tma  18 balanced  19 n_rcp_fast (refined reciprocals).
+ * March counts exclude operations on constants and parameters only (hoisted by the compiler). */
 typedef struct acs_variant_info {
-    float feats[ACS_VARIANT_NFEAT];  /* static features; names from acs_variant_feature_name */
-    double cost;                     /* the paper's cost of the extracted DAG, shared nodes once */
+    float feats[ACS_VARIANT_NFEAT];
+    double cost;                     /* the paper's cost of the extracted DAG(s), shared nodes once */
     int enodes, eclasses, iterations;
-    int block_x;                     /* threads along x of the variant's 256-thread block */
+    int scope;                       /* acs_scope */
+    int block_x, block_y;            /* block shape (iteration scope: block_x x 256/block_x threads) */
+    int flags;                       /* march scope: ACS_TILE_BALANCED / ACS_TILE_TMA it is built for */
     long long src_bytes, dag_bytes;  /* buffer sizes needed (including the terminating 0) */
 } acs_variant_info;
 
-acs_status acs_variant_generate(unsigned long long seed, int index, char *src, size_t src_len, char *dag,
+acs_status acs_variant_generate(unsigned long long seed, int index, int scope, char *src, size_t src_len, char *dag,
                                 size_t dag_len, acs_variant_info *info);
 const char *acs_variant_feature_name(int i);
 
-/* Compile a generated variant with NVRTC for sm_103a (FMA contraction off) and load it.
- * ACS_ERR_UNSUPPORTED if libnvrtc cannot be loaded. `regs` receives the register count. */
-typedef struct acs_variant_module *acs_variant_handle;
-acs_status acs_variant_build(const char *src, int block_x, acs_variant_handle *out, int *regs);
-/* Run a loaded variant on a grid (same geometry rules as acs_rhs_plain). */
+/* Compile a generated variant (src and the info acs_variant_generate filled) with NVRTC for
+ * sm_103a (FMA contraction off, so the extracted operations are what runs) and load it on the
+ * current device; `regs` receives the register count. With out == NULL the source is only
+ * compiled (no device is needed), to check it. ACS_ERR_UNSUPPORTED if libnvrtc cannot be
+ * loaded, ACS_ERR_INVALID with the compiler's log in acs_last_error() if compilation fails. */
+acs_status acs_variant_build(const char *src, const acs_variant_info *info, acs_variant_handle *out, int *regs);
+/* Run a loaded variant on a grid (same geometry rules as acs_rhs_plain); a march-scope variant
+ * runs with its own tile and flags (as acs_rhs_saturated with tile NULL). */
 acs_status acs_variant_launch(acs_variant_handle h, const double *U, double *R, const acs_grid *g,
                               const acs_rhs_params *p, acs_stream stream);
 void acs_variant_free(acs_variant_handle h);
@@ -428,9 +469,11 @@ acs_status acs_rcp_selftest(const double *x, double *y, long long n, acs_stream 
 /* Reason for the calling thread's most recent failed call ("" if none). */
 const char *acs_last_error(void);
 
-/* ABI version of this library (major * 100 + minor): 101 adds ACS_TILE_BALANCED,
- * ACS_TILE_TMA and acs_wait_timeouts to 100, 102 adds acs_wait_selftest; calls valid under
- * 100 give the same results. */
+/* ABI version of this library (major * 100 + minor). 200: acs_rhs_saturated takes a variant,
+ * acs_variant_generate a scope and acs_variant_build the variant's info, acs_variant_info has
+ * 20 features and the scope, block and flags fields; the ranker's gradient, model files, the
+ * FP64 rate probe and the reciprocal self-test are added. (1xx: 101 added ACS_TILE_BALANCED,
+ * ACS_TILE_TMA and acs_wait_timeouts, 102 acs_wait_selftest.) */
 int acs_abi_version(void);
 
 #ifdef __cplusplus

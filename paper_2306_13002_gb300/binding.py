@@ -57,12 +57,14 @@ class BatchPlan(ctypes.Structure):
 KIND_RHS, KIND_STENCIL = 0, 1
 TILE_BALANCED = 1  # acs_tile.flags: one block per resident slot, equal (column, plane) shares
 TILE_TMA = 2       # acs_tile.flags: planes staged by TMA tensor copies (single-grid saturated kernels)
-VARIANT_NFEAT = 16
+VARIANT_NFEAT = 20
+SCOPE_ITERATION, SCOPE_MARCH = 0, 1   # acs_scope
 
 
 class VariantInfo(ctypes.Structure):
     _fields_ = [("feats", ctypes.c_float * VARIANT_NFEAT), ("cost", ctypes.c_double), ("enodes", ctypes.c_int),
-                ("eclasses", ctypes.c_int), ("iterations", ctypes.c_int), ("block_x", ctypes.c_int),
+                ("eclasses", ctypes.c_int), ("iterations", ctypes.c_int), ("scope", ctypes.c_int),
+                ("block_x", ctypes.c_int), ("block_y", ctypes.c_int), ("flags", ctypes.c_int),
                 ("src_bytes", ctypes.c_longlong), ("dag_bytes", ctypes.c_longlong)]
 
 
@@ -98,7 +100,7 @@ def lib() -> ctypes.CDLL:
             p, st = ctypes.c_void_p, ctypes.c_int
             L.acs_rhs_plain.argtypes = [p, p, ctypes.POINTER(Grid), ctypes.POINTER(RhsParams), p]
             L.acs_rhs_saturated.argtypes = [p, p, ctypes.POINTER(Grid), ctypes.POINTER(RhsParams),
-                                            ctypes.POINTER(Tile), p]
+                                            ctypes.POINTER(Tile), p, p]
             L.acs_rhs_form.argtypes = [p, p, ctypes.POINTER(Grid), ctypes.POINTER(RhsParams), st,
                                        ctypes.POINTER(Tile), p]
             L.acs_stencil_plain.argtypes = [p, p, p, ctypes.POINTER(Grid), ctypes.POINTER(ctypes.c_double), p]
@@ -125,11 +127,11 @@ def lib() -> ctypes.CDLL:
             for f in ("acs_batch_prepare", "acs_batch_launch", "acs_batch_run_static", "acs_autotune_rhs", "acs_autotune_stencil",
                       "acs_autotune_batch", "acs_tune_cache_save", "acs_tune_cache_load"):
                 getattr(L, f).restype = st
-            L.acs_variant_generate.argtypes = [ctypes.c_ulonglong, st, ctypes.c_char_p, ctypes.c_size_t,
+            L.acs_variant_generate.argtypes = [ctypes.c_ulonglong, st, st, ctypes.c_char_p, ctypes.c_size_t,
                                                ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(VariantInfo)]
             L.acs_variant_feature_name.argtypes = [st]
             L.acs_variant_feature_name.restype = ctypes.c_char_p
-            L.acs_variant_build.argtypes = [ctypes.c_char_p, st, ctypes.POINTER(ctypes.c_void_p),
+            L.acs_variant_build.argtypes = [ctypes.c_char_p, ctypes.POINTER(VariantInfo), ctypes.POINTER(ctypes.c_void_p),
                                             ctypes.POINTER(ctypes.c_int)]
             L.acs_variant_launch.argtypes = [p, p, p, G, ctypes.POINTER(RhsParams), p]
             L.acs_variant_free.argtypes = [p]
@@ -245,10 +247,14 @@ def acs_rhs_plain(U, R, gamma: float = 1.4, eps: float = 0.25, h=(1.0, 1.0, 1.0)
 
 
 def acs_rhs_saturated(U, R, gamma: float = 1.4, eps: float = 0.25, h=(1.0, 1.0, 1.0), halo: int = 2,
-                      tile=None, stream=None) -> None:
+                      tile=None, variant=None, stream=None) -> None:
+    """Saturated RHS; `variant` None for the library's kernel, or a march-scope `Variant`."""
     g = grid_for(U, R, halo, 5)
     pr = _params(gamma, eps, h)
-    _check(lib().acs_rhs_saturated(U.data_ptr(), R.data_ptr(), ctypes.byref(g), ctypes.byref(pr), _tile(tile),
+    vh = variant.handle if variant is not None else None
+    if variant is not None and not vh:
+        raise ValueError("variant has been closed")
+    _check(lib().acs_rhs_saturated(U.data_ptr(), R.data_ptr(), ctypes.byref(g), ctypes.byref(pr), _tile(tile), vh,
                                    _stream_ptr(stream)), "acs_rhs_saturated")
 
 
@@ -432,26 +438,28 @@ def acs_variant_feature_names() -> list[str]:
     return [lib().acs_variant_feature_name(i).decode() for i in range(VARIANT_NFEAT)]
 
 
-def acs_variant_generate(seed: int, index: int):
-    """(cuda_source, dag_text, VariantInfo) of rewriter variant `index` (host only)."""
+def acs_variant_generate(seed: int, index: int, scope: int = SCOPE_ITERATION):
+    """(cuda_source, dag_text, VariantInfo) of rewriter variant `index` in `scope` (host only)."""
     info = VariantInfo()
-    _check(lib().acs_variant_generate(int(seed), int(index), None, 0, None, 0, ctypes.byref(info)),
+    _check(lib().acs_variant_generate(int(seed), int(index), int(scope), None, 0, None, 0, ctypes.byref(info)),
            "acs_variant_generate")
     src = ctypes.create_string_buffer(int(info.src_bytes))
     dag = ctypes.create_string_buffer(int(info.dag_bytes))
-    _check(lib().acs_variant_generate(int(seed), int(index), src, len(src), dag, len(dag), ctypes.byref(info)),
-           "acs_variant_generate")
+    _check(lib().acs_variant_generate(int(seed), int(index), int(scope), src, len(src), dag, len(dag),
+                                      ctypes.byref(info)), "acs_variant_generate")
     return src.value.decode(), dag.value.decode(), info
 
 
 class Variant:
     """A compiled, loaded rewriter variant (freed with close())."""
 
-    def __init__(self, src: str, block_x: int):
+    def __init__(self, src: str, info: VariantInfo):
         h, regs = ctypes.c_void_p(), ctypes.c_int()
-        _check(lib().acs_variant_build(src.encode(), int(block_x), ctypes.byref(h), ctypes.byref(regs)),
+        _check(lib().acs_variant_build(src.encode(), ctypes.byref(info), ctypes.byref(h), ctypes.byref(regs)),
                "acs_variant_build")
         self.handle, self.regs = h, regs.value
+        self.scope, self.block = int(info.scope), (int(info.block_x), int(info.block_y))
+        self.flags = int(info.flags)
 
     def launch(self, U, R, gamma=1.4, eps=0.25, h=(1.0, 1.0, 1.0), halo=2, stream=None):
         g = grid_for(U, R, halo, 5)

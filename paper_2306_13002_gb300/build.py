@@ -38,7 +38,8 @@ def _sources() -> list[str]:
 
 
 def _deps() -> list[str]:
-    return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h")) + [__file__]
+    return (_sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) +
+            glob.glob(os.path.join(INCLUDE, "*.h")) + [__file__])
 
 
 def up_to_date() -> bool:

@@ -398,11 +398,22 @@ acs_status acs_rhs_plain(const double* U, double* R, const acs_grid* g, const ac
 }
 
 acs_status acs_rhs_saturated(const double* U, double* R, const acs_grid* g, const acs_rhs_params* p,
-                             const acs_tile* tile, acs_stream stream) {
+                             const acs_tile* tile, acs_variant_handle variant, acs_stream stream) {
     Geom geo;
     RhsConst k;
     acs_status st = check_rhs(U, R, g, p, geo, k);
     if (st != ACS_OK) return st;
+    if (variant) {
+        if (variant->scope != ACS_SCOPE_MARCH)
+            return fail(ACS_ERR_INVALID, "acs_rhs_saturated takes march-scope variants only");
+        if (tile && (tile->bx != variant->bx || tile->by != variant->by || tile->flags != variant->flags))
+            return fail(ACS_ERR_INVALID, "tile %dx%d flags %d does not match the variant's %dx%d flags %d", tile->bx,
+                        tile->by, tile->flags, variant->bx, variant->by, variant->flags);
+        if (tile && tile->kchunk < 0) return fail(ACS_ERR_INVALID, "kchunk must be >= 0");
+        if ((geo.ny + variant->by - 1) / variant->by > 65535 && !(variant->flags & ACS_TILE_BALANCED))
+            return fail(ACS_ERR_INVALID, "ny too large for a z-chunk launch of this variant");
+        return variant_launch_march(variant, U, R, geo, k, tile ? tile->kchunk : 0, (cudaStream_t)stream);
+    }
     acs_tile t;
     st = check_tile(tile, kDefaultRhsTile, rhs_tile_supported, t, ACS_KIND_RHS, &geo);
     if (st != ACS_OK) return st;
@@ -438,7 +449,7 @@ acs_status acs_rhs_saturated_host(const double* U, double* R, const acs_grid* g,
 acs_status acs_rhs_form(const double* U, double* R, const acs_grid* g, const acs_rhs_params* p, int form,
                         const acs_tile* tile, acs_stream stream) {
     if (form == ACS_FORM_AS_WRITTEN) return acs_rhs_plain(U, R, g, p, stream);
-    if (form == ACS_FORM_SATURATED) return acs_rhs_saturated(U, R, g, p, tile, stream);
+    if (form == ACS_FORM_SATURATED) return acs_rhs_saturated(U, R, g, p, tile, nullptr, stream);
     if (form < ACS_FORM_CSE || form > ACS_FORM_ACCSAT) return fail(ACS_ERR_INVALID, "unknown RHS form %d", form);
     Geom geo;
     RhsConst k;
@@ -582,10 +593,12 @@ acs_status acs_autotune_batch(const acs_batch_item* items, int n, int kind, cons
                       best_ms);
 }
 
-acs_status acs_variant_generate(unsigned long long seed, int index, char* src, size_t src_len, char* dag,
+acs_status acs_variant_generate(unsigned long long seed, int index, int scope, char* src, size_t src_len, char* dag,
                                 size_t dag_len, acs_variant_info* info) {
     if (index < 0) return fail(ACS_ERR_INVALID, "variant index must be >= 0");
+    if (scope != ACS_SCOPE_ITERATION && scope != ACS_SCOPE_MARCH) return fail(ACS_ERR_INVALID, "unknown scope %d", scope);
     try {
+        if (scope == ACS_SCOPE_MARCH) return variant_generate_march(seed, index, src, src_len, dag, dag_len, info);
         return variant_generate(seed, index, src, src_len, dag, dag_len, info);
     } catch (...) {
         return fail(ACS_ERR_INVALID, "variant generation failed (out of memory?)");
@@ -594,15 +607,16 @@ acs_status acs_variant_generate(unsigned long long seed, int index, char* src, s
 
 const char* acs_variant_feature_name(int i) { return variant_feature_name(i); }
 
-acs_status acs_variant_build(const char* src, int block_x, acs_variant_handle* out, int* regs) {
-    if (!src || !out) return fail(ACS_ERR_INVALID, "src or out is NULL");
-    *out = nullptr;
-    return variant_build(src, block_x, out, regs);
+acs_status acs_variant_build(const char* src, const acs_variant_info* info, acs_variant_handle* out, int* regs) {
+    if (!src || !info) return fail(ACS_ERR_INVALID, "src or info is NULL");
+    if (out) *out = nullptr;
+    return variant_build(src, *info, out, regs);
 }
 
 acs_status acs_variant_launch(acs_variant_handle h, const double* U, double* R, const acs_grid* g,
                               const acs_rhs_params* p, acs_stream stream) {
     if (!h) return fail(ACS_ERR_INVALID, "variant handle is NULL");
+    if (h->scope == ACS_SCOPE_MARCH) return acs_rhs_saturated(U, R, g, p, nullptr, h, stream);
     Geom geo;
     RhsConst k;
     acs_status st = check_rhs(U, R, g, p, geo, k);
@@ -755,6 +769,6 @@ acs_status acs_wait_selftest(unsigned int* timeouts, acs_stream stream) {
     return ACS_OK;
 }
 
-int acs_abi_version(void) { return 103; }
+int acs_abi_version(void) { return 200; }
 
 }  // extern "C"

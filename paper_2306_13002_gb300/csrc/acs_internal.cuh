@@ -13,7 +13,9 @@
 struct acs_variant_module {
     cudaLibrary_t lib;
     cudaKernel_t kern;
-    int bx;
+    int scope;   // acs_scope
+    int bx, by;
+    int flags;   // march scope: ACS_TILE_TMA / ACS_TILE_BALANCED of the compiled kernel
     int regs;
 };
 
@@ -76,8 +78,14 @@ int tune_cache_size();
 // Rewriter, variants and ranker.
 acs_status variant_generate(unsigned long long seed, int index, char* src, size_t src_len, char* dag, size_t dag_len,
                             acs_variant_info* info);
+acs_status variant_generate_march(unsigned long long seed, int index, char* src, size_t src_len, char* dag,
+                                  size_t dag_len, acs_variant_info* info);
 const char* variant_feature_name(int i);
-acs_status variant_build(const char* src, int block_x, acs_variant_module** out, int* regs);
+acs_status variant_build(const char* src, const acs_variant_info& info, acs_variant_module** out, int* regs);
+// Shared memory of a march-scope variant's kernel (ring, flux planes, constants, mbarriers).
+size_t variant_march_smem_bytes(int bx, int by);
+acs_status variant_launch_march(acs_variant_module* m, const double* U, double* R, const Geom& g, const RhsConst& k,
+                                int kchunk, cudaStream_t s);
 acs_status variant_launch(acs_variant_module* m, const double* U, double* R, const Geom& g, const RhsConst& k,
                           cudaStream_t s);
 void variant_free(acs_variant_module* m);

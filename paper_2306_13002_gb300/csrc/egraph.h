@@ -325,67 +325,69 @@ class Rewriter {
         }
     }
 
-    // F_COLLECT: for every maximal sum (an ADD or SUB e-class that no ADD/SUB/NEG node uses), flatten
-    // it through the first ADD/SUB/NEG node of each class into signed terms coefficient * leaf
-    // (a leaf's coefficient is the constant factor of its first MUL(constant, x) node, else 1),
-    // add up the coefficients of equal leaves (only when the sum is exact), drop zero terms, group
-    // the leaves by equal coefficient and add  sum_g c_g * (sum of the leaves of g)  to the class,
-    // groups and leaves in order of first appearance. Only sums where terms merged are rewritten.
-    // Returns the number of classes that gained a collected form.
-    int collect(const std::vector<std::vector<int>>& cn, size_t node_limit) {
+    // F_COLLECT: like-term collection over the current cheapest program. `best` is the e-node
+    // extraction picks per class under positive operation costs, so following it never cycles
+    // (an e-class may hold x + 0 = x after folding). For every maximal sum (a class whose best
+    // node is an ADD or SUB and that no best ADD/SUB/NEG node uses), flatten it through best
+    // ADD/SUB/NEG nodes into signed terms coefficient * leaf (a leaf whose best node is
+    // MUL(constant, x) has that coefficient, else 1), add up the coefficients of equal leaves
+    // (only where the sum is exact), drop zero terms, group the leaves by equal coefficient and
+    // add  sum_g c_g * (sum of the leaves of g)  to the class, groups and leaves in order of first
+    // appearance. Only sums where terms merged are rewritten. Returns the classes rewritten.
+    int collect(const std::vector<std::vector<int>>& cn, const std::vector<int>& best, size_t node_limit) {
         const int nc = g.nclasses;
-        std::vector<char> inner(nc, 0);
-        for (const Node& n : g.nodes)
-            if (n.op == ADD || n.op == SUB || n.op == NEG) {
-                inner[g.find(n.a)] = 1;
-                if (n.op != NEG) inner[g.find(n.b)] = 1;
-            }
-        auto first_of = [&](int cls, std::initializer_list<int> ops) -> const Node* {
-            for (int ni : cn[g.find(cls)])
-                for (int op : ops)
-                    if (g.nodes[ni].op == op) return &g.nodes[ni];
-            return nullptr;
+        auto bnode = [&](int cls) -> const Node* {
+            const int b = best[g.find(cls)];
+            return b >= 0 ? &g.nodes[b] : nullptr;
         };
+        std::vector<char> inner(nc, 0);
+        for (int c = 0; c < nc; ++c) {
+            if (g.find(c) != c) continue;
+            const Node* n = bnode(c);
+            if (n && (n->op == ADD || n->op == SUB || n->op == NEG)) {
+                inner[g.find(n->a)] = 1;
+                if (n->op != NEG) inner[g.find(n->b)] = 1;
+            }
+        }
         std::vector<int> roots;
-        for (int c = 0; c < nc; ++c)
-            if (g.find(c) == c && !inner[c] && first_of(c, {ADD, SUB})) roots.push_back(c);
+        for (int c = 0; c < nc; ++c) {
+            if (g.find(c) != c || inner[c]) continue;
+            const Node* n = bnode(c);
+            if (n && (n->op == ADD || n->op == SUB)) roots.push_back(c);
+        }
         int changed = 0;
         for (int root : roots) {
             if (g.nodes.size() >= node_limit) break;
             std::vector<std::pair<int, double>> terms;   // (leaf class, signed coefficient)
+            std::vector<std::pair<int, double>> stack{{root, 1.0}};
             bool overflow = false;
-            std::vector<std::tuple<int, double, int>> stack{{root, 1.0, 0}};
-            while (!stack.empty()) {
-                auto [cls, sign, depth] = stack.back();
+            while (!stack.empty() && !overflow) {
+                auto [cls, sign] = stack.back();
                 stack.pop_back();
-                const Node* sn = depth < 32 ? first_of(cls, {ADD, SUB, NEG}) : nullptr;
-                if (sn && terms.size() + stack.size() < 96) {
-                    // push right child first so the left subtree's terms come first
+                const Node* sn = bnode(cls);
+                if (sn && (sn->op == ADD || sn->op == SUB || sn->op == NEG)) {
+                    if (terms.size() + stack.size() > 96) {
+                        overflow = true;
+                        break;
+                    }
                     if (sn->op == NEG) {
-                        stack.push_back({sn->a, -sign, depth + 1});
-                    } else {
-                        stack.push_back({sn->b, sn->op == SUB ? -sign : sign, depth + 1});
-                        stack.push_back({sn->a, sign, depth + 1});
+                        stack.push_back({sn->a, -sign});
+                    } else {   // right child first so the left subtree's terms come first
+                        stack.push_back({sn->b, sn->op == SUB ? -sign : sign});
+                        stack.push_back({sn->a, sign});
                     }
                     continue;
                 }
-                if (sn) overflow = true;
                 double v;
                 if (g.const_value(cn, cls, &v) && v == 0.0) continue;   // x + 0
                 double coef = sign;
                 int leaf = g.find(cls);
-                for (int ni : cn[g.find(cls)]) {
-                    const Node& m = g.nodes[ni];
-                    if (m.op != MUL) continue;
+                if (sn && sn->op == MUL) {
                     double cv;
-                    if (g.const_value(cn, m.a, &cv) && !g.const_value(cn, m.b, &v)) {
-                        coef = sign * cv, leaf = g.find(m.b);
-                        break;
-                    }
-                    if (g.const_value(cn, m.b, &cv) && !g.const_value(cn, m.a, &v)) {
-                        coef = sign * cv, leaf = g.find(m.a);
-                        break;
-                    }
+                    if (g.const_value(cn, sn->a, &cv) && !g.const_value(cn, sn->b, &v))
+                        coef = sign * cv, leaf = g.find(sn->b);
+                    else if (g.const_value(cn, sn->b, &cv) && !g.const_value(cn, sn->a, &v))
+                        coef = sign * cv, leaf = g.find(sn->a);
                 }
                 terms.push_back({leaf, coef});
             }
@@ -409,8 +411,7 @@ class Rewriter {
                          }),
                          merged.end());
             if (merged.empty()) continue;
-            // group by |coefficient| and sign
-            std::vector<std::pair<double, std::vector<int>>> groups;
+            std::vector<std::pair<double, std::vector<int>>> groups;   // by signed coefficient
             for (auto& t : merged) {
                 bool done = false;
                 for (auto& gr : groups)
@@ -462,31 +463,6 @@ class Rewriter {
     }
 };
 
-// Runs the families in the given order, iteration after iteration, until nothing changes, the
-// iteration limit is reached or the e-graph holds node_limit e-nodes. Returns the iterations run.
-inline int saturate(EGraph& g, const std::vector<int>& fams, int max_iters, size_t node_limit) {
-    Rewriter rw(g);
-    int iters = 0;
-    for (iters = 0; iters < max_iters && g.nodes.size() < node_limit; ++iters) {
-        int changes = 0;
-        for (int f : fams) {
-            auto cn = g.class_nodes();
-            if (f == F_COLLECT) {
-                changes += rw.collect(cn, node_limit);
-            } else {
-                std::vector<Pending> ps;
-                std::vector<int> unions;
-                rw.match(f, cn, ps, unions);
-                changes += rw.apply(ps, unions, node_limit);
-            }
-            g.rebuild();
-            if (g.nodes.size() >= node_limit) break;
-        }
-        if (changes == 0) break;
-    }
-    return iters;
-}
-
 // ------------------------------------------------------------------ extraction
 
 struct Extracted {
@@ -522,6 +498,31 @@ inline Extracted extract(EGraph& g, const double* opcost) {
         if (!changed) break;
     }
     return ex;
+}
+
+// Runs the families in the given order, iteration after iteration, until nothing changes, the
+// iteration limit is reached or the e-graph holds node_limit e-nodes. Returns the iterations run.
+inline int saturate(EGraph& g, const std::vector<int>& fams, int max_iters, size_t node_limit) {
+    Rewriter rw(g);
+    int iters = 0;
+    for (iters = 0; iters < max_iters && g.nodes.size() < node_limit; ++iters) {
+        int changes = 0;
+        for (int f : fams) {
+            auto cn = g.class_nodes();
+            if (f == F_COLLECT) {
+                changes += rw.collect(cn, extract(g, kPaperCost).best, node_limit);
+            } else {
+                std::vector<Pending> ps;
+                std::vector<int> unions;
+                rw.match(f, cn, ps, unions);
+                changes += rw.apply(ps, unions, node_limit);
+            }
+            g.rebuild();
+            if (g.nodes.size() >= node_limit) break;
+        }
+        if (changes == 0) break;
+    }
+    return iters;
 }
 
 }  // namespace rw

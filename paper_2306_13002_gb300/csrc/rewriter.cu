@@ -220,6 +220,7 @@ Program codegen(EGraph& g, const Extracted& ex, const Body& body, bool bulk, boo
     f[13] = (float)bx;
     f[14] = 0.f;  // registers, filled after compilation
     f[15] = (float)(n_arith + 9 * (cnt[DIV] + cnt[RCP]));
+    f[16] = (float)(256 / bx);   // block_y; tma, balanced, n_rcp_fast stay 0
     pr.cost = cost;
 
     // CUDA source
@@ -299,8 +300,8 @@ Program codegen(EGraph& g, const Extracted& ex, const Body& body, bool bulk, boo
 }  // namespace rw
 
 static const char* kFeatureNames[ACS_VARIANT_NFEAT] = {
-    "paper_cost", "n_add", "n_mul", "n_fma", "n_div", "n_neg", "n_load", "n_load_x",
-    "n_load_yz", "n_nodes", "max_live", "bulk", "pipe", "block_x", "regs", "dp_ops_est"};
+    "paper_cost", "n_add", "n_mul", "n_fma", "n_div", "n_neg", "n_load", "n_load_x", "n_load_yz", "n_nodes",
+    "max_live", "bulk", "pipe", "block_x", "regs", "dp_ops_est", "block_y", "tma", "balanced", "n_rcp_fast"};
 
 const char* variant_feature_name(int i) { return (i >= 0 && i < ACS_VARIANT_NFEAT) ? kFeatureNames[i] : ""; }
 
@@ -345,7 +346,10 @@ acs_status variant_generate(unsigned long long seed, int index, char* src, size_
         for (int c = 0; c < g.nclasses; ++c) ncls += g.find(c) == c;
         info->eclasses = ncls;
         info->iterations = iters;
+        info->scope = ACS_SCOPE_ITERATION;
         info->block_x = bx;
+        info->block_y = 256 / bx;
+        info->flags = 0;
         info->src_bytes = (long long)pr.src.size() + 1;
         info->dag_bytes = (long long)pr.dag.size() + 1;
     }

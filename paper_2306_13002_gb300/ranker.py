@@ -36,14 +36,27 @@ def spearman(a, b) -> float:
     return float((ra * rb).sum() / den) if den > 0 else 0.0
 
 
-def generate(n: int, seed: int = inputs.SEED_VARIANTS):
-    """Host rewriter output for variants 0..n-1: list of dicts (src, dag, feats, cost, ...)."""
+def generate(n: int, seed: int = inputs.SEED_VARIANTS, scope: int = binding.SCOPE_MARCH):
+    """Host rewriter output for variants 0..n-1 of `scope`: list of dicts (src, dag, feats, ...)."""
     out = []
     for i in range(n):
-        src, dag, info = binding.acs_variant_generate(seed, i)
-        out.append({"index": i, "src": src, "dag": dag, "feats": np.array(info.feats[:], dtype=np.float32),
-                    "cost": info.cost, "block_x": info.block_x, "enodes": info.enodes,
+        src, dag, info = binding.acs_variant_generate(seed, i, scope)
+        out.append({"index": i, "src": src, "dag": dag, "info": info,
+                    "feats": np.array(info.feats[:], dtype=np.float32), "cost": info.cost,
+                    "block": (info.block_x, info.block_y), "flags": info.flags, "enodes": info.enodes,
                     "iterations": info.iterations})
+    return out
+
+
+def distinct(variants):
+    """The variants whose generated source is new (the first of each identical group): identical
+    sources have identical features and run the same code, so they must not be split between the
+    training and the test set."""
+    seen, out = set(), []
+    for v in variants:
+        if v["src"] not in seen:
+            seen.add(v["src"])
+            out.append(v)
     return out
 
 
@@ -52,7 +65,7 @@ def compile_all(variants, threads: int | None = None):
     threads = threads or min(16, os.cpu_count() or 4)
 
     def build(v):
-        return binding.Variant(v["src"], v["block_x"])
+        return binding.Variant(v["src"], v["info"])
 
     with cf.ThreadPoolExecutor(max_workers=threads) as ex:
         mods = list(ex.map(build, variants))
@@ -80,21 +93,40 @@ def time_all(variants, U, R, reps: int = 5, stream=None):
     return variants
 
 
-def study(n_variants: int = 512, n_train: int = 400, n: int = 256, seed: int = inputs.SEED_VARIANTS,
-          hidden: int = 64, epochs: int = 3000, lr: float = 3e-3, reps: int = 5) -> dict:
-    """Generate, compile and time the variants at n^3, train on n_train, evaluate on the rest."""
+def max_err_over_tol(R, ref) -> float:
+    """max |R - ref| / (1e-12 |ref| + 1e-14) over all points (<= 1: within the parity tolerance)."""
+    return float(((R - ref).abs() / (1e-12 * ref.abs() + 1e-14)).max())
+
+
+def study(n_variants: int = 512, n_train: int | None = None, n: int = 256, seed: int = inputs.SEED_VARIANTS,
+          hidden: int = 64, epochs: int = 3000, lr: float = 3e-3, reps: int = 5,
+          scope: int = binding.SCOPE_MARCH, check: bool = True) -> dict:
+    """Generate `n_variants` variants, keep the distinct ones, compile and time them at n^3, train the
+    MLP on a random n_train of them (default: 400/512 of the distinct variants) and rank the rest,
+    by the MLP and by the paper's analytical cost. With `check`, every variant's output is compared
+    with the library's saturated kernel (itself parity-checked against the oracle) at n^3."""
     import torch
-    vs = compile_all(generate(n_variants, seed))
+    vs_all = generate(n_variants, seed, scope)
+    vs = distinct(vs_all)
+    nd = len(vs)
+    if n_train is None:
+        n_train = int(round(nd * 400 / 512))
+    n_train = max(2, min(n_train, nd - 2))
+    compile_all(vs)
     U = torch.from_numpy(inputs.rhs_field(n, halo=2, seed=inputs.SEED_RHS_LARGE)).cuda()
     R = torch.empty((5, n, n, n), dtype=torch.float64, device="cuda")
     time_all(vs, U, R, reps=reps)
-    # consistency of one variant's output with the library's ACCSAT form (sanity only)
-    Rc = torch.empty_like(R)
-    binding.acs_rhs_form(U, Rc, "accsat")
-    vs[1]["module"].launch(U, R)
-    torch.cuda.synchronize()
-    rel = float(((R - Rc).abs() / (1e-12 * Rc.abs() + 1e-14)).max())
-    perm = np.random.default_rng(seed).permutation(n_variants)
+    worst = None
+    if check:
+        ref = torch.empty_like(R)
+        binding.acs_rhs_saturated(U, ref)
+        worst = 0.0
+        for v in vs:
+            R.fill_(float("nan"))
+            v["module"].launch(U, R)
+            worst = max(worst, max_err_over_tol(R, ref))
+        del ref
+    perm = np.random.default_rng(seed).permutation(nd)
     tr, te = perm[:n_train], perm[n_train:]
     F = len(vs[0]["feats"])
     X = torch.from_numpy(np.stack([v["feats"] for v in vs])).cuda()
@@ -124,17 +156,20 @@ def study(n_variants: int = 512, n_train: int = 400, n: int = 256, seed: int = i
     all_ms = np.array([v["ms"] for v in vs])
     for v in vs:
         v["module"].close()
+    pm, pa, pb = vs[te[order_m[0]]], vs[te[order_a[0]]], vs[te[int(np.argmin(times_te))]]
     return {
-        "variants": n_variants, "train": n_train, "test": n_variants - n_train, "grid": n,
-        "hidden": hidden, "epochs": epochs, "lr": lr, "train_ms": train_ms,
+        "scope": "march" if scope == binding.SCOPE_MARCH else "iteration",
+        "variants_generated": n_variants, "variants_distinct": nd, "train": int(len(tr)), "test": int(len(te)),
+        "grid": n, "hidden": hidden, "epochs": epochs, "lr": lr, "train_ms": train_ms,
         "spearman_mlp_test": spearman(pred, times_te),
         "spearman_mlp_train": spearman(pred_tr, times_tr),
         "spearman_analytical_test": spearman(cost, times_te),
         "best_test_ms": best, "mlp_pick_ms": pick_m, "analytical_pick_ms": pick_a,
         "mlp_pick_over_best": pick_m / best, "analytical_pick_over_best": pick_a / best,
         "all_ms_min": float(all_ms.min()), "all_ms_median": float(np.median(all_ms)),
-        "all_ms_max": float(all_ms.max()), "variant1_vs_accsat_err_over_tol": rel,
-        "distinct_sources": len({v["src"] for v in vs}),
-        "mlp_pick_index": int(te[order_m[0]]), "analytical_pick_index": int(te[order_a[0]]),
-        "best_test_index": int(te[int(np.argmin(times_te))]),
+        "all_ms_max": float(all_ms.max()), "max_err_over_tol_vs_saturated": worst,
+        "mlp_pick_index": int(pm["index"]), "analytical_pick_index": int(pa["index"]),
+        "best_test_index": int(pb["index"]),
+        "mlp_pick_shape": [*pm["block"], pm["flags"]],
+        "best_all_index": int(vs[int(np.argmin(all_ms))]["index"]),
     }

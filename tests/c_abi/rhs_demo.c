@@ -56,7 +56,7 @@ int main(int argc, char **argv) {
     const acs_grid g = {nx, ny, nz, halo, X, X * Y, X * Y * Z, nx, (long long)nx * ny, (long long)nx * ny * nz};
     const acs_rhs_params p = {1.4, 0.25, {1.0, 1.0, 1.0}};
 
-    acs_status st = acs_rhs_saturated(dU, dR, &g, &p, NULL, NULL);
+    acs_status st = acs_rhs_saturated(dU, dR, &g, &p, NULL, NULL, NULL);
     if (st != ACS_OK) return fail_status("acs_rhs_saturated", st);
     if (cudaMemcpy(R, dR, n_out * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return 1;
     if (write_file(argv[5], R, n_out)) return 1;
@@ -66,7 +66,7 @@ int main(int argc, char **argv) {
     if (cudaMemcpy(R, dR, n_out * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return 1;
     if (write_file(argv[6], R, n_out)) return 1;
 
-    if (acs_rhs_saturated(NULL, dR, &g, &p, NULL, NULL) != ACS_ERR_INVALID) {
+    if (acs_rhs_saturated(NULL, dR, &g, &p, NULL, NULL, NULL) != ACS_ERR_INVALID) {
         fprintf(stderr, "a NULL input was not rejected\n");
         return 1;
     }

@@ -57,7 +57,8 @@ def _params(h=(1.0, 1.0, 1.0)):
 def _call_rhs(lib, U, R, g, p, sat=False, tile=None):
     if sat:
         t = ctypes.byref(binding.Tile(*tile)) if tile else None
-        return lib.acs_rhs_saturated(U, R, ctypes.byref(g) if g else None, ctypes.byref(p) if p else None, t, None)
+        return lib.acs_rhs_saturated(U, R, ctypes.byref(g) if g else None, ctypes.byref(p) if p else None, t, None,
+                                     None)
     return lib.acs_rhs_plain(U, R, ctypes.byref(g) if g else None, ctypes.byref(p) if p else None, None)
 
 
