@@ -851,7 +851,7 @@ def run_ours(args) -> None:
         from paper_2306_13002_gb300 import ranker
         torch.cuda.empty_cache()
         study = bench_ranker(binding, ranker)
-        keys = ("variants_generated", "variants_distinct", "train", "test", "spearman_mlp_test",
+        keys = ("variants_generated", "variants_distinct", "train", "test", "fast_weight", "spearman_mlp_test",
                 "spearman_analytical_test", "best_test_ms", "mlp_pick_ms", "analytical_pick_ms", "mlp_pick_over_best",
                 "analytical_pick_over_best", "all_ms_min", "all_ms_median", "all_ms_max",
                 "max_err_over_tol_vs_saturated", "mlp_pick_index", "mlp_pick_shape", "best_all_index", "wall_s")

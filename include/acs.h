@@ -378,19 +378,22 @@ void acs_variant_free(acs_variant_handle h);
 size_t acs_ranker_param_count(int n_feats, int hidden);
 size_t acs_ranker_workspace_bytes(int n, int n_feats, int hidden);
 /* Train on n variants: feats (device, n x n_feats floats), times_ms (device, n floats > 0);
- * writes the model into params (device, acs_ranker_param_count floats). Full-batch Adam on
- * the squared error of the standardised log time; deterministic for a given seed. epochs == 0
- * writes the initial model only (standardisation statistics and seeded initial weights).
+ * writes the model into params (device, acs_ranker_param_count floats). Full-batch Adam on the
+ * weighted squared error of the standardised log time t: sample weight exp(-fast_weight t_i)
+ * normalised to mean 1 (0 = plain mean squared error; larger values weigh the fast variants,
+ * which decide the pick, more; at most 8). Deterministic for a given seed. epochs == 0 writes
+ * the initial model only (standardisation statistics and seeded initial weights).
  * Parameter layout (floats): mu[F] sd[F] tmu tsd W1[H][F] b1[H] W2[H][H] b2[H] w3[H] b3. */
 acs_status acs_ranker_train(const float *feats, const float *times_ms, int n, int n_feats, int hidden, int epochs,
-                            float lr, unsigned long long seed, float *params, void *ws, size_t ws_bytes,
-                            acs_stream stream);
-/* Gradient of the training loss (mean squared error of the standardised log time, with the
- * statistics stored in params) with respect to every parameter at `params`, without updating
- * them: grad (device, acs_ranker_param_count floats; 0 for mu, sd, tmu, tsd). Same kernels as
- * one training epoch. ws as for acs_ranker_train. Synchronises `stream`. */
+                            float lr, float fast_weight, unsigned long long seed, float *params, void *ws,
+                            size_t ws_bytes, acs_stream stream);
+/* Gradient of that training loss (with the statistics stored in params and the same sample
+ * weights) with respect to every parameter at `params`, without updating them: grad (device,
+ * acs_ranker_param_count floats; 0 for mu, sd, tmu, tsd). Same kernels as one training epoch.
+ * ws as for acs_ranker_train. Synchronises `stream`. */
 acs_status acs_ranker_gradient(const float *feats, const float *times_ms, int n, int n_feats, int hidden,
-                               const float *params, float *grad, void *ws, size_t ws_bytes, acs_stream stream);
+                               const float *params, float fast_weight, float *grad, void *ws, size_t ws_bytes,
+                               acs_stream stream);
 typedef struct acs_ranker_model {
     int n_feats;
     int hidden;

@@ -140,8 +140,8 @@ def lib() -> ctypes.CDLL:
             L.acs_ranker_param_count.restype = ctypes.c_size_t
             L.acs_ranker_workspace_bytes.argtypes = [st, st, st]
             L.acs_ranker_workspace_bytes.restype = ctypes.c_size_t
-            L.acs_ranker_train.argtypes = [p, p, st, st, st, st, ctypes.c_float, ctypes.c_ulonglong, p, p,
-                                           ctypes.c_size_t, p]
+            L.acs_ranker_train.argtypes = [p, p, st, st, st, st, ctypes.c_float, ctypes.c_float, ctypes.c_ulonglong,
+                                           p, p, ctypes.c_size_t, p]
             L.acs_variant_rank.argtypes = [p, st, st, ctypes.POINTER(RankerModel), p, ctypes.POINTER(ctypes.c_int),
                                            ctypes.POINTER(ctypes.c_float), p]
             for f in ("acs_variant_generate", "acs_variant_build", "acs_variant_launch", "acs_ranker_train",
@@ -161,7 +161,7 @@ def lib() -> ctypes.CDLL:
             L.acs_wait_timeouts.restype = st
             L.acs_wait_selftest.argtypes = [ctypes.POINTER(ctypes.c_uint), ctypes.c_void_p]
             L.acs_wait_selftest.restype = st
-            L.acs_ranker_gradient.argtypes = [p, p, st, st, st, p, p, p, ctypes.c_size_t, p]
+            L.acs_ranker_gradient.argtypes = [p, p, st, st, st, p, ctypes.c_float, p, p, ctypes.c_size_t, p]
             L.acs_ranker_save.argtypes = [ctypes.c_char_p, ctypes.POINTER(RankerModel)]
             L.acs_ranker_load.argtypes = [ctypes.c_char_p, p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int),
                                           ctypes.POINTER(ctypes.c_int)]
@@ -487,12 +487,13 @@ def acs_ranker_workspace_bytes(n: int, n_feats: int, hidden: int) -> int:
     return int(lib().acs_ranker_workspace_bytes(int(n), int(n_feats), int(hidden)))
 
 
-def acs_ranker_train(feats, times_ms, params, ws, hidden=64, epochs=3000, lr=3e-3, seed=13006, stream=None):
+def acs_ranker_train(feats, times_ms, params, ws, hidden=64, epochs=3000, lr=3e-3, seed=13006, fast_weight=0.0,
+                     stream=None):
     """Train the MLP on device tensors feats (n x F float32) and times_ms (n float32)."""
     _on_device(feats, times_ms, params, ws)
     n, F = feats.shape
     _check(lib().acs_ranker_train(feats.data_ptr(), times_ms.data_ptr(), int(n), int(F), int(hidden), int(epochs),
-                                  float(lr), int(seed), params.data_ptr(), ws.data_ptr(),
+                                  float(lr), float(fast_weight), int(seed), params.data_ptr(), ws.data_ptr(),
                                   ws.numel() * ws.element_size(), _stream_ptr(stream)), "acs_ranker_train")
 
 
@@ -511,12 +512,12 @@ def acs_variant_rank(feats, params=None, hidden=64, scores_dev=None, stream=None
     return list(order), list(score)
 
 
-def acs_ranker_gradient(feats, times_ms, params, grad, ws, hidden=64, stream=None) -> None:
+def acs_ranker_gradient(feats, times_ms, params, grad, ws, hidden=64, fast_weight=0.0, stream=None) -> None:
     """Loss gradient at `params` (no update) into the device tensor `grad` (P floats)."""
     _on_device(feats, times_ms, params, grad, ws)
     n, F = feats.shape
     _check(lib().acs_ranker_gradient(feats.data_ptr(), times_ms.data_ptr(), int(n), int(F), int(hidden),
-                                     params.data_ptr(), grad.data_ptr(), ws.data_ptr(),
+                                     params.data_ptr(), float(fast_weight), grad.data_ptr(), ws.data_ptr(),
                                      ws.numel() * ws.element_size(), _stream_ptr(stream)), "acs_ranker_gradient")
 
 

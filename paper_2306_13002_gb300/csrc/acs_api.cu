@@ -633,13 +633,14 @@ size_t acs_ranker_param_count(int n_feats, int hidden) { return ranker_param_cou
 size_t acs_ranker_workspace_bytes(int n, int n_feats, int hidden) { return ranker_ws_bytes(n, n_feats, hidden); }
 
 acs_status acs_ranker_train(const float* feats, const float* times_ms, int n, int n_feats, int hidden, int epochs,
-                            float lr, unsigned long long seed, float* params, void* ws, size_t ws_bytes,
-                            acs_stream stream) {
+                            float lr, float fast_weight, unsigned long long seed, float* params, void* ws,
+                            size_t ws_bytes, acs_stream stream) {
     if (!feats || !times_ms || !params || !ws) return fail(ACS_ERR_INVALID, "NULL pointer");
     if (n < 2 || n_feats < 1 || n_feats > 1024 || hidden < 1 || hidden > 1024 || epochs < 0 || !(lr > 0.f))
         return fail(ACS_ERR_INVALID, "bad ranker training size or rate");
+    if (!(fast_weight >= 0.f && fast_weight <= 8.f)) return fail(ACS_ERR_INVALID, "fast_weight must be in [0, 8]");
     if (!aligned(ws, 16) || !aligned(params, 4) || !aligned(feats, 4)) return fail(ACS_ERR_ALIGN, "misaligned buffer");
-    return ranker_train(feats, times_ms, n, n_feats, hidden, epochs, lr, seed, params, ws, ws_bytes,
+    return ranker_train(feats, times_ms, n, n_feats, hidden, epochs, lr, fast_weight, seed, params, ws, ws_bytes,
                         (cudaStream_t)stream);
 }
 
@@ -675,13 +676,16 @@ acs_status acs_variant_rank(const float* feats, int n, int n_feats, const acs_ra
 }
 
 acs_status acs_ranker_gradient(const float* feats, const float* times_ms, int n, int n_feats, int hidden,
-                               const float* params, float* grad, void* ws, size_t ws_bytes, acs_stream stream) {
+                               const float* params, float fast_weight, float* grad, void* ws, size_t ws_bytes,
+                               acs_stream stream) {
     if (!feats || !times_ms || !params || !grad || !ws) return fail(ACS_ERR_INVALID, "NULL pointer");
     if (n < 1 || n_feats < 1 || n_feats > 1024 || hidden < 1 || hidden > 1024)
         return fail(ACS_ERR_INVALID, "bad ranker sizes");
+    if (!(fast_weight >= 0.f && fast_weight <= 8.f)) return fail(ACS_ERR_INVALID, "fast_weight must be in [0, 8]");
     if (!aligned(ws, 16) || !aligned(params, 4) || !aligned(feats, 4) || !aligned(grad, 4))
         return fail(ACS_ERR_ALIGN, "misaligned buffer");
-    return ranker_gradient(feats, times_ms, n, n_feats, hidden, params, grad, ws, ws_bytes, (cudaStream_t)stream);
+    return ranker_gradient(feats, times_ms, n, n_feats, hidden, params, fast_weight, grad, ws, ws_bytes,
+                           (cudaStream_t)stream);
 }
 
 acs_status acs_ranker_save(const char* path, const acs_ranker_model* model) {

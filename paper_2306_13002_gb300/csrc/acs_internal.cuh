@@ -92,12 +92,13 @@ void variant_free(acs_variant_module* m);
 size_t ranker_param_count(int F, int H);
 size_t ranker_ws_bytes(int n, int F, int H);
 acs_status ranker_train(const float* feats, const float* times, int n, int F, int H, int epochs, float lr,
-                        unsigned long long seed, float* params, void* ws, size_t ws_bytes, cudaStream_t s);
+                        float fast_weight, unsigned long long seed, float* params, void* ws, size_t ws_bytes,
+                        cudaStream_t s);
 acs_status ranker_predict(const float* feats, int n, int F, int H, const float* params, float* scores, cudaStream_t s);
 acs_status analytical_scores(const float* feats, int n, int F, float* scores, cudaStream_t s);
 acs_status ranker_denormalise(const float* params, int F, int H, std::vector<float>& y);
 acs_status ranker_gradient(const float* feats, const float* times, int n, int F, int H, const float* params,
-                           float* grad, void* ws, size_t ws_bytes, cudaStream_t s);
+                           float fast_weight, float* grad, void* ws, size_t ws_bytes, cudaStream_t s);
 acs_status ranker_save(const char* path, const float* params, int F, int H);
 acs_status ranker_load(const char* path, float* params, size_t capacity, int* F, int* H);
 

@@ -166,7 +166,12 @@ class EGraph {
 // F_COLLECT is this library's: like-term collection of a whole sum, an identity over the reals
 // that computer-algebra systems apply as a normal form; an equality-saturation schedule reaches
 // it only through a combinatorial number of ASSOC/COMM steps.
-enum Family : int { F_FMA = 0, F_COMM, F_ASSOC, F_FOLD, F_DIV, F_DISTRIB, F_SUBNEG, F_COLLECT, NFAM };
+// F_EXPAND (distributive expansion, the direction of distributivity the factoring rules of
+// F_DISTRIB do not take) and F_NEGPUSH (negation moved into products, sums and FMAs: -(a b) =
+// (-a) b, -(a b + c) = (-a) b + (-c), -(a + b) = (-a) - b, -(a - b) = b - a) are also this
+// library's; both are identities over the reals and exact in IEEE arithmetic for negation.
+enum Family : int { F_FMA = 0, F_COMM, F_ASSOC, F_FOLD, F_DIV, F_DISTRIB, F_SUBNEG, F_COLLECT, F_EXPAND, F_NEGPUSH,
+                    NFAM };
 constexpr int NFAM_PAPER = F_COLLECT;
 
 // Exact constant folding only: the folded double must equal the exact result.
@@ -187,6 +192,8 @@ struct Pending {
     int64_t payload;
     int inner_op = -1, ia = -1, ib = -1;  // optional child built first, placed in slot inner_slot
     int inner_slot = -1;
+    int inner2_op = -1, ja = -1, jb = -1;  // an optional second such child, in slot inner2_slot
+    int inner2_slot = -1;
 };
 
 class Rewriter {
@@ -321,6 +328,48 @@ class Rewriter {
                         for (auto* m : f1) unions.push_back(cls), unions.push_back(m->a);
                     }
                     break;
+                case F_EXPAND:
+                    if (n.op == MUL) {
+                        for (int side = 0; side < 2; ++side) {   // A * (X1 +- X2), (X1 +- X2) * A
+                            const int x = side ? n.a : n.b, A = side ? n.b : n.a;
+                            for (int sop : {ADD, SUB})
+                                if (has(x, sop, f1))
+                                    for (auto* m : f1) {
+                                        Pending p{cls, sop, -2, -2, -1, 0};
+                                        p.inner_op = MUL, p.ia = A, p.ib = m->a, p.inner_slot = 0;
+                                        p.inner2_op = MUL, p.ja = A, p.jb = m->b, p.inner2_slot = 1;
+                                        out.push_back(p);
+                                    }
+                        }
+                    }
+                    break;
+                case F_NEGPUSH:
+                    if (n.op == NEG) {
+                        if (has(n.a, MUL, f1))   // -(A B) -> (-A) B
+                            for (auto* m : f1) {
+                                Pending p{cls, MUL, -2, m->b, -1, 0};
+                                p.inner_op = NEG, p.ia = m->a, p.inner_slot = 0;
+                                out.push_back(p);
+                            }
+                        if (has(n.a, FMA, f1))   // -(A B + C) -> (-A) B + (-C)
+                            for (auto* m : f1) {
+                                Pending p{cls, FMA, -2, m->b, -2, 0};
+                                p.inner_op = NEG, p.ia = m->a, p.inner_slot = 0;
+                                p.inner2_op = NEG, p.ja = m->c, p.inner2_slot = 2;
+                                out.push_back(p);
+                            }
+                        if (has(n.a, ADD, f1))   // -(A + B) -> (-A) - B
+                            for (auto* m : f1) {
+                                Pending p{cls, SUB, -2, m->b, -1, 0};
+                                p.inner_op = NEG, p.ia = m->a, p.inner_slot = 0;
+                                out.push_back(p);
+                            }
+                        if (has(n.a, SUB, f1))   // -(A - B) -> B - A
+                            for (auto* m : f1) out.push_back({cls, SUB, m->b, m->a, -1, 0});
+                        if (has(n.a, NEG, f1))   // -(-A) -> A
+                            for (auto* m : f1) unions.push_back(cls), unions.push_back(m->a);
+                    }
+                    break;
             }
         }
     }
@@ -453,6 +502,8 @@ class Rewriter {
                     inner = g.add(p.inner_op, p.ia, p.ib);
                 args[p.inner_slot] = inner;
             }
+            if (p.inner2_slot >= 0)
+                args[p.inner2_slot] = p.inner2_op == NEG ? g.add(NEG, p.ja) : g.add(p.inner2_op, p.ja, p.jb);
             const size_t before = g.nodes.size();
             const int nc = g.add(p.op, args[0], args[1], args[2], p.payload);
             if (g.merge(nc, p.cls) || g.nodes.size() != before) ++changes;
@@ -496,6 +547,137 @@ inline Extracted extract(EGraph& g, const double* opcost) {
             }
         }
         if (!changed) break;
+    }
+    return ex;
+}
+
+// Extraction for a loop body, used by the march scope:
+//  - an operation whose operands are all constants or parameters (an e-class computable from
+//    them alone) is computed once, outside the loop over points, and costs nothing;
+//  - the cost of a program is its DAG cost: every class it uses is paid once, however many
+//    operations share it, which is the quantity the paper's extraction minimises (Sec. IV-B,
+//    solved there as an ILP). Here a greedy tree-cost extraction is improved by local search:
+//    each class of the program tries each of its e-nodes, and a change is kept when the DAG
+//    cost of the whole program drops (and the choice stays acyclic), until no change helps or
+//    `rounds` passes are done.
+inline Extracted extract_dag(EGraph& g, const double* opcost, const std::vector<int>& outs, int rounds = 4) {
+    auto cn = g.class_nodes();
+    const int nc = g.nclasses;
+    // classes computable from constants and parameters alone
+    std::vector<char> inv(nc, 0);
+    for (bool changed = true; changed;) {
+        changed = false;
+        for (int c = 0; c < nc; ++c) {
+            if (g.find(c) != c || inv[c]) continue;
+            for (int ni : cn[c]) {
+                const Node& n = g.nodes[ni];
+                const int ar = arity(n.op);
+                bool all = n.op == CONST || n.op == PARAM || ar > 0;
+                if (n.op == LOAD || n.op == FLUX) all = false;
+                if (ar > 0) all = all && inv[g.find(n.a)];
+                if (ar > 1) all = all && inv[g.find(n.b)];
+                if (ar > 2) all = all && inv[g.find(n.c)];
+                if (all) {
+                    inv[c] = 1;
+                    changed = true;
+                    break;
+                }
+            }
+        }
+    }
+    auto own = [&](const Node& n) -> double {
+        const int ar = arity(n.op);
+        if (ar == 0) return n.op == CONST ? 0.0 : opcost[n.op];
+        bool all = inv[g.find(n.a)] && (ar < 2 || inv[g.find(n.b)]) && (ar < 3 || inv[g.find(n.c)]);
+        return all ? 0.0 : opcost[n.op];
+    };
+    // greedy tree-cost start
+    std::vector<double> cost(nc, INFINITY);
+    Extracted ex;
+    ex.best.assign(nc, -1);
+    for (int pass = 0; pass < 200; ++pass) {
+        bool changed = false;
+        for (int c = 0; c < nc; ++c) {
+            if (g.find(c) != c) continue;
+            for (int ni : cn[c]) {
+                const Node& n = g.nodes[ni];
+                double sc = own(n);
+                const int ar = arity(n.op);
+                if (ar > 0) sc += cost[g.find(n.a)];
+                if (ar > 1) sc += cost[g.find(n.b)];
+                if (ar > 2) sc += cost[g.find(n.c)];
+                if (sc < cost[c] - 1e-9) {
+                    cost[c] = sc;
+                    ex.best[c] = ni;
+                    changed = true;
+                }
+            }
+        }
+        if (!changed) break;
+    }
+    for (int r : outs)
+        if (ex.best[g.find(r)] < 0) return ex;
+    // DAG cost of the program under the current choice; -1 if the choice is cyclic
+    std::vector<int> mark(nc, 0);
+    int stamp = 0;
+    auto dag_cost = [&](double* out) -> bool {
+        ++stamp;
+        double total = 0.0;
+        std::vector<std::pair<int, int>> st;   // iterative DFS; mark -stamp = on the path
+        for (int r : outs) {
+            const int root = g.find(r);
+            if (mark[root] == stamp) continue;
+            st.push_back({root, 0});
+            mark[root] = -stamp;   // on path
+            while (!st.empty()) {
+                auto& top = st.back();
+                const int c = top.first;
+                const Node& n = g.nodes[ex.best[c]];
+                const int ar = arity(n.op);
+                if (top.second < ar) {
+                    const int ch = g.find(top.second == 0 ? n.a : top.second == 1 ? n.b : n.c);
+                    ++top.second;
+                    if (mark[ch] == -stamp) return false;   // cycle
+                    if (mark[ch] != stamp) {
+                        if (ex.best[ch] < 0) return false;
+                        mark[ch] = -stamp;
+                        st.push_back({ch, 0});
+                    }
+                    continue;
+                }
+                mark[c] = stamp;
+                total += own(n);
+                st.pop_back();
+            }
+        }
+        *out = total;
+        return true;
+    };
+    double cur;
+    if (!dag_cost(&cur)) return ex;
+    for (int round = 0; round < rounds; ++round) {
+        bool improved = false;
+        // the classes the program uses now
+        std::vector<int> used;
+        for (int c = 0; c < nc; ++c)
+            if (g.find(c) == c && mark[c] == stamp) used.push_back(c);
+        for (int c : used) {
+            const int keep = ex.best[c];
+            for (int ni : cn[c]) {
+                if (ni == keep || ni == ex.best[c]) continue;
+                const int prev = ex.best[c];
+                ex.best[c] = ni;
+                double t;
+                if (dag_cost(&t) && t < cur - 1e-9) {
+                    cur = t;
+                    improved = true;
+                } else {
+                    ex.best[c] = prev;
+                }
+            }
+        }
+        dag_cost(&cur);   // refresh the marks of the used classes
+        if (!improved) break;
     }
     return ex;
 }

@@ -8,7 +8,9 @@
 //
 // Model: x (F features, standardised with the training set's mean and deviation) ->
 // h1 = relu(W1 x + b1) (H) -> h2 = relu(W2 h1 + b2) (H) -> y = w3 . h2 + b3, the
-// standardised log of the run time. Loss: mean squared error over the training set.
+// standardised log of the run time. Loss: weighted mean squared error over the training set,
+// sample weight w_i = exp(-a t_i) / mean_j exp(-a t_j) of its standardised log time t_i (a = 0:
+// plain MSE; a > 0 weighs the fast variants, which decide the pick, more).
 // Optimiser: Adam (Kingma & Ba, 2015; beta1 0.9, beta2 0.999, eps 1e-8), full batch.
 // Parameter buffer (floats): mu[F] sd[F] tmu tsd W1[H*F] b1[H] W2[H*H] b2[H] w3[H] b3.
 // Per epoch three kernels: forward (a block per sample, a thread per hidden unit),
@@ -81,14 +83,14 @@ __global__ void mlp_forward(const float* __restrict__ X, const float* __restrict
     }
 }
 
-__global__ void mlp_backward_sample(const float* __restrict__ T, const float* __restrict__ prm, int F, int H, int n,
-                                    const float* __restrict__ H1, const float* __restrict__ H2,
+__global__ void mlp_backward_sample(const float* __restrict__ T, const float* __restrict__ Wt, const float* __restrict__ prm,
+                                    int F, int H, int n, const float* __restrict__ H1, const float* __restrict__ H2,
                                     const float* __restrict__ Y, float* DH1, float* DH2, float* DY) {
     extern __shared__ float sh[];
     float* dh2 = sh;
     const int s = blockIdx.x, j = threadIdx.x;
     const Layout L(F, H);
-    const float dy = 2.f * (Y[s] - T[s]) / (float)n;
+    const float dy = 2.f * Wt[s] * (Y[s] - T[s]) / (float)n;
     if (j == 0) DY[s] = dy;
     if (j < H) {
         const float g = H2[(size_t)s * H + j] > 0.f ? dy * prm[L.w3 + j] : 0.f;
@@ -157,9 +159,9 @@ __global__ void copy_column(const float* __restrict__ X, int F, int col, int n, 
 }
 
 struct Ws {
-    float *H1, *H2, *Y, *DH1, *DH2, *DY, *T, *m, *v;
+    float *H1, *H2, *Y, *DH1, *DH2, *DY, *T, *W, *m, *v;
 };
-size_t ws_floats(int n, int H, size_t P) { return 4 * (size_t)n * H + 3 * (size_t)n + 2 * P; }
+size_t ws_floats(int n, int H, size_t P) { return 4 * (size_t)n * H + 4 * (size_t)n + 2 * P; }
 Ws carve(float* base, int n, int H, size_t P) {
     Ws w;
     w.H1 = base;
@@ -169,9 +171,20 @@ Ws carve(float* base, int n, int H, size_t P) {
     w.Y = w.DH2 + (size_t)n * H;
     w.DY = w.Y + n;
     w.T = w.DY + n;
-    w.m = w.T + n;
+    w.W = w.T + n;
+    w.m = w.W + n;
     w.v = w.m + P;
     return w;
+}
+
+// Sample weights of the loss: exp(-a t_i) normalised to mean 1 (t: standardised log times).
+std::vector<float> loss_weights(const std::vector<float>& tstd, float a) {
+    std::vector<double> w(tstd.size());
+    double sum = 0.0;
+    for (size_t i = 0; i < w.size(); ++i) sum += (w[i] = std::exp(-(double)a * tstd[i]));
+    std::vector<float> out(w.size());
+    for (size_t i = 0; i < w.size(); ++i) out[i] = (float)(w[i] * (double)w.size() / sum);
+    return out;
 }
 
 }  // namespace
@@ -182,7 +195,8 @@ size_t ranker_ws_bytes(int n, int F, int H) {
 }
 
 acs_status ranker_train(const float* feats, const float* times, int n, int F, int H, int epochs, float lr,
-                        unsigned long long seed, float* params, void* ws, size_t ws_bytes, cudaStream_t s) {
+                        float fast_weight, unsigned long long seed, float* params, void* ws, size_t ws_bytes,
+                        cudaStream_t s) {
     const Layout L(F, H);
     if (ws_bytes < ranker_ws_bytes(n, F, H)) return fail(ACS_ERR_WORKSPACE, "ranker workspace too small");
     // Standardisation statistics and the initial weights are computed on the host.
@@ -227,8 +241,10 @@ acs_status ranker_train(const float* feats, const float* times, int n, int F, in
     for (size_t q = 0; q < (size_t)H * H; ++q) p[L.W2 + q] = (float)((2 * uni() - 1) * a2);
     for (int q = 0; q < H; ++q) p[L.w3 + q] = (float)((2 * uni() - 1) * a2);
     Ws w = carve(static_cast<float*>(ws), n, H, L.P);
+    const std::vector<float> wts = loss_weights(tstd, fast_weight);
     if (cudaMemcpyAsync(params, p.data(), L.P * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(w.T, tstd.data(), n * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(w.W, wts.data(), n * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(w.m, 0, 2 * L.P * 4, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
         return launch_status("ranker_train: uploading the initial model");
     const int tb = H < 32 ? 32 : ((H + 31) / 32) * 32;
@@ -236,7 +252,7 @@ acs_status ranker_train(const float* feats, const float* times, int n, int F, in
     const unsigned pg = (unsigned)((L.P + 255) / 256);
     for (int e = 1; e <= epochs; ++e) {   // epochs == 0: the initial model only
         mlp_forward<<<n, tb, sh_f, s>>>(feats, params, F, H, w.H1, w.H2, w.Y, 1);
-        mlp_backward_sample<<<n, tb, sh_b, s>>>(w.T, params, F, H, n, w.H1, w.H2, w.Y, w.DH1, w.DH2, w.DY);
+        mlp_backward_sample<<<n, tb, sh_b, s>>>(w.T, w.W, params, F, H, n, w.H1, w.H2, w.Y, w.DH1, w.DH2, w.DY);
         mlp_grad_adam<<<pg, 256, 0, s>>>(feats, w.H1, w.H2, w.DH1, w.DH2, w.DY, params, w.m, w.v, F, H, n, e, lr,
                                          nullptr);
     }
@@ -244,7 +260,7 @@ acs_status ranker_train(const float* feats, const float* times, int n, int F, in
 }
 
 acs_status ranker_gradient(const float* feats, const float* times, int n, int F, int H, const float* params,
-                           float* grad, void* ws, size_t ws_bytes, cudaStream_t s) {
+                           float fast_weight, float* grad, void* ws, size_t ws_bytes, cudaStream_t s) {
     const Layout L(F, H);
     if (ws_bytes < ranker_ws_bytes(n, F, H)) return fail(ACS_ERR_WORKSPACE, "ranker workspace too small");
     // The target: the standardised log time, with the statistics stored in the model.
@@ -260,12 +276,15 @@ acs_status ranker_gradient(const float* feats, const float* times, int n, int F,
         tstd[i] = (float)((std::log(ht[i]) - st[0]) / st[1]);
     }
     Ws w = carve(static_cast<float*>(ws), n, H, L.P);
-    if (cudaMemcpyAsync(w.T, tstd.data(), n * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    const std::vector<float> wts = loss_weights(tstd, fast_weight);
+    if (cudaMemcpyAsync(w.T, tstd.data(), n * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(w.W, wts.data(), n * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return launch_status("ranker_gradient: uploading targets");
     const int tb = H < 32 ? 32 : ((H + 31) / 32) * 32;
     float* prm = const_cast<float*>(params);   // read only when grad is set
     mlp_forward<<<n, tb, sizeof(float) * (F + 2 * H), s>>>(feats, params, F, H, w.H1, w.H2, w.Y, 1);
-    mlp_backward_sample<<<n, tb, sizeof(float) * H, s>>>(w.T, params, F, H, n, w.H1, w.H2, w.Y, w.DH1, w.DH2, w.DY);
+    mlp_backward_sample<<<n, tb, sizeof(float) * H, s>>>(w.T, w.W, params, F, H, n, w.H1, w.H2, w.Y, w.DH1, w.DH2,
+                                                          w.DY);
     mlp_grad_adam<<<(unsigned)((L.P + 255) / 256), 256, 0, s>>>(feats, w.H1, w.H2, w.DH1, w.DH2, w.DY, prm, w.m, w.v,
                                                                  F, H, n, 1, 0.f, grad);
     if (cudaStreamSynchronize(s) != cudaSuccess) return launch_status("ranker_gradient kernels");

@@ -318,7 +318,10 @@ acs_status variant_generate_march(unsigned long long seed, int index, char* src,
         auto draw_fams = [&]() {
             std::vector<int> fams;
             for (int f = 0; f < NFAM; ++f) {
-                const double pon = (f == F_FMA || f == F_FOLD || f == F_DIV) ? 0.8 : f == F_COLLECT ? 0.7 : 0.55;
+                const double pon = (f == F_FMA || f == F_FOLD || f == F_DIV) ? 0.8
+                                   : f == F_COLLECT                          ? 0.7
+                                   : (f == F_EXPAND || f == F_NEGPUSH)       ? 0.5
+                                                                             : 0.55;
                 if (rng.uniform() < pon) fams.push_back(f);
             }
             for (int k = (int)fams.size() - 1; k > 0; --k) std::swap(fams[k], fams[rng.below(k + 1)]);
@@ -343,12 +346,12 @@ acs_status variant_generate_march(unsigned long long seed, int index, char* src,
         tile = kTiles[u < 0.3 ? 0 : u < 0.55 ? 1 : u < 0.7 ? 2 : u < 0.8 ? 3 : u < 0.9 ? 4 : 5];
         flags = (rng.uniform() < 0.8 ? ACS_TILE_TMA : 0) | (rng.uniform() < 0.7 ? ACS_TILE_BALANCED : 0);
     }
-    const Extracted exf = extract(gf, opcost);
-    const Extracted exc = extract(gc, opcost);
     std::vector<int> fouts, couts;
     for (int d = 0; d < 3; ++d)
         for (int s = 0; s < 4; ++s) fouts.push_back(fb.out[d][s]);
     for (int s = 0; s < 5; ++s) couts.push_back(cb.root[s]);
+    const Extracted exf = extract_dag(gf, opcost, fouts);
+    const Extracted exc = extract_dag(gc, opcost, couts);
     for (int r : fouts)
         if (exf.best[gf.find(r)] < 0) return fail(ACS_ERR_INVALID, "flux extraction failed");
     for (int r : couts)

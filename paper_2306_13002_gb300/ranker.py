@@ -100,10 +100,11 @@ def max_err_over_tol(R, ref) -> float:
 
 def study(n_variants: int = 512, n_train: int | None = None, n: int = 256, seed: int = inputs.SEED_VARIANTS,
           hidden: int = 64, epochs: int = 3000, lr: float = 3e-3, reps: int = 5,
-          scope: int = binding.SCOPE_MARCH, check: bool = True) -> dict:
+          scope: int = binding.SCOPE_MARCH, check: bool = True, fast_weight: float = 1.0) -> dict:
     """Generate `n_variants` variants, keep the distinct ones, compile and time them at n^3, train the
-    MLP on a random n_train of them (default: 400/512 of the distinct variants) and rank the rest,
-    by the MLP and by the paper's analytical cost. With `check`, every variant's output is compared
+    MLP on a random n_train of them (default: 400/512 of the distinct variants; squared error of the
+    standardised log time weighted by exp(-fast_weight t), so the fast variants that decide the
+    pick weigh more) and rank the rest, by the MLP and by the paper's analytical cost. With `check`, every variant's output is compared
     with the library's saturated kernel (itself parity-checked against the oracle) at n^3."""
     import torch
     vs_all = generate(n_variants, seed, scope)
@@ -141,7 +142,8 @@ def study(n_variants: int = 512, n_train: int | None = None, n: int = 256, seed:
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record()
-    binding.acs_ranker_train(Xtr, Ttr, params, ws, hidden=hidden, epochs=epochs, lr=lr, seed=seed)
+    binding.acs_ranker_train(Xtr, Ttr, params, ws, hidden=hidden, epochs=epochs, lr=lr, seed=seed,
+                             fast_weight=fast_weight)
     t1.record()
     torch.cuda.synchronize()
     train_ms = t0.elapsed_time(t1)
@@ -160,7 +162,7 @@ def study(n_variants: int = 512, n_train: int | None = None, n: int = 256, seed:
     return {
         "scope": "march" if scope == binding.SCOPE_MARCH else "iteration",
         "variants_generated": n_variants, "variants_distinct": nd, "train": int(len(tr)), "test": int(len(te)),
-        "grid": n, "hidden": hidden, "epochs": epochs, "lr": lr, "train_ms": train_ms,
+        "grid": n, "hidden": hidden, "epochs": epochs, "lr": lr, "fast_weight": fast_weight, "train_ms": train_ms,
         "spearman_mlp_test": spearman(pred, times_te),
         "spearman_mlp_train": spearman(pred_tr, times_tr),
         "spearman_analytical_test": spearman(cost, times_te),

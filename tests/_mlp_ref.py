@@ -3,7 +3,8 @@ reference the GPU tests compare the hand-written training and inference kernels 
 
 Model (the parameter layout of acs.h): x = (features - mu) / sd, h1 = relu(W1 x + b1),
 h2 = relu(W2 h1 + b2), y = w3 . h2 + b3; target t = (log time - tmu) / tsd; loss = mean of
-(y - t)^2 over the samples. Test infrastructure only.
+w_i (y - t)^2 over the samples, w_i = exp(-a t_i) normalised to mean 1 (a = fast_weight).
+Test infrastructure only.
 """
 import numpy as np
 
@@ -31,18 +32,24 @@ def np_forward(P, X):
     return x, h1, h2, h2 @ P["w3"] + P["b3"]
 
 
-def np_loss(P, X, T):
+def np_weights(t, fast_weight):
+    """Sample weights exp(-a t_i) normalised to mean 1 (a = 0: all ones)."""
+    w = np.exp(-fast_weight * t)
+    return w * len(w) / w.sum()
+
+
+def np_loss(P, X, T, fast_weight=0.0):
     t = (np.log(T) - P["tmu"]) / P["tsd"]
-    return float(np.mean((np_forward(P, X)[3] - t) ** 2))
+    return float(np.mean(np_weights(t, fast_weight) * (np_forward(P, X)[3] - t) ** 2))
 
 
-def np_grad(P, X, T):
-    """Analytic gradient of the mean squared error of the standardised log time (float64),
-    flattened in the buffer layout (zeros for the fixed statistics)."""
+def np_grad(P, X, T, fast_weight=0.0):
+    """Analytic gradient of the weighted mean squared error of the standardised log time
+    (float64), flattened in the buffer layout (zeros for the fixed statistics)."""
     n = X.shape[0]
     x, h1, h2, y = np_forward(P, X)
     t = (np.log(T) - P["tmu"]) / P["tsd"]
-    dy = 2.0 * (y - t) / n
+    dy = 2.0 * np_weights(t, fast_weight) * (y - t) / n
     g_w3 = h2.T @ dy
     g_b3 = dy.sum()
     dh2 = np.outer(dy, P["w3"]) * (h2 > 0)

@@ -224,8 +224,10 @@ def test_probe_and_selftest_entry_points_reject_bad_arguments(lib):
 
 
 def test_ranker_gradient_and_model_files_reject_bad_arguments(lib, tmp_path):
-    assert lib.acs_ranker_gradient(None, FAKE_R, 8, 4, 16, FAKE_U, FAKE_R, FAKE_U, 1 << 20, None) == 1
-    assert lib.acs_ranker_gradient(FAKE_U, FAKE_R, 0, 4, 16, FAKE_U, FAKE_R, FAKE_U, 1 << 20, None) == 1
+    assert lib.acs_ranker_gradient(None, FAKE_R, 8, 4, 16, FAKE_U, 1.0, FAKE_R, FAKE_U, 1 << 20, None) == 1
+    assert lib.acs_ranker_gradient(FAKE_U, FAKE_R, 0, 4, 16, FAKE_U, 1.0, FAKE_R, FAKE_U, 1 << 20, None) == 1
+    assert lib.acs_ranker_gradient(FAKE_U, FAKE_R, 8, 4, 16, FAKE_U, -1.0, FAKE_R, FAKE_U, 1 << 20, None) == 1
+    assert lib.acs_ranker_train(FAKE_U, FAKE_R, 8, 4, 16, 10, 1e-3, 9.0, 1, FAKE_R, FAKE_U, 1 << 20, None) == 1
     assert lib.acs_ranker_save(None, None) == 1
     bad = tmp_path / "bad.model"
     bad.write_text("acs-ranker-model 1\n3 4 999\n")

@@ -172,12 +172,15 @@ def test_small_study_end_to_end():
 
 # ------------------------------------------------------------------ numerical reference of the MLP
 
+FW = 1.0   # the loss weighting the study uses
+
+
 def _train(X, T, H, epochs, lr=1e-2, seed=3):
     n, F = X.shape
     Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
     params = torch.empty(binding.acs_ranker_param_count(F, H), dtype=torch.float32, device="cuda")
     ws = torch.empty(binding.acs_ranker_workspace_bytes(n, F, H) // 4 + 4, dtype=torch.float32, device="cuda")
-    binding.acs_ranker_train(Xd, Td, params, ws, hidden=H, epochs=epochs, lr=lr, seed=seed)
+    binding.acs_ranker_train(Xd, Td, params, ws, hidden=H, epochs=epochs, lr=lr, seed=seed, fast_weight=FW)
     torch.cuda.synchronize()
     return params, Xd, Td, ws
 
@@ -201,9 +204,9 @@ def test_forward_gradient_and_adam_match_float64_reference():
     assert np.allclose(pred, ref_ms, rtol=1e-5)
     # gradient at p0
     g0 = torch.empty_like(p0)
-    binding.acs_ranker_gradient(Xd, Td, p0, g0, ws, hidden=H)
+    binding.acs_ranker_gradient(Xd, Td, p0, g0, ws, hidden=H, fast_weight=FW)
     g0n = g0.cpu().numpy().astype(np.float64)
-    gref = _np_grad(P0, X.astype(np.float64), T.astype(np.float64))
+    gref = _np_grad(P0, X.astype(np.float64), T.astype(np.float64), FW)
     assert np.abs(gref).max() > 1e-3
     assert np.allclose(g0n, gref, rtol=1e-3, atol=1e-4 * np.abs(gref).max())
     # one Adam epoch: m = (1-b1) g, v = (1-b2) g^2, bias-corrected step lr * g / (|g| + 1e-8)
@@ -219,9 +222,9 @@ def test_forward_gradient_and_adam_match_float64_reference():
     assert np.array_equal(p1n[:2 * F + 2], flat0[:2 * F + 2])   # statistics are not trained
     # second epoch: the moments carry over, bias correction with step 2
     g1 = torch.empty_like(p1)
-    binding.acs_ranker_gradient(Xd, Td, p1, g1, ws, hidden=H)
+    binding.acs_ranker_gradient(Xd, Td, p1, g1, ws, hidden=H, fast_weight=FW)
     g1n = g1.cpu().numpy().astype(np.float64)
-    assert np.allclose(g1n, _np_grad(_unpack(p1n, F, H), X.astype(np.float64), T.astype(np.float64)),
+    assert np.allclose(g1n, _np_grad(_unpack(p1n, F, H), X.astype(np.float64), T.astype(np.float64), FW),
                        rtol=1e-3, atol=1e-4 * np.abs(gref).max())
     m = b1 * m + (1 - b1) * g1n
     v = b2 * v + (1 - b2) * g1n ** 2

@@ -3,10 +3,13 @@ its analytic gradient against central differences, and its forward pass against 
 hand-written loop over one sample."""
 import numpy as np
 
+import pytest
+
 from _mlp_ref import np_forward, np_grad, np_loss, small_problem, unpack
 
 
-def test_numpy_reference_gradient_matches_central_differences():
+@pytest.mark.parametrize("fw", [0.0, 1.0])
+def test_numpy_reference_gradient_matches_central_differences(fw):
     """The analytic gradient of the reference equals central differences of its loss."""
     X, T, H = small_problem()
     rng = np.random.default_rng(5)
@@ -17,14 +20,14 @@ def test_numpy_reference_gradient_matches_central_differences():
          "b2": rng.uniform(-0.1, 0.1, H), "w3": rng.uniform(-0.5, 0.5, H), "b3": 0.05}
     flat = np.concatenate([P["mu"], P["sd"], [P["tmu"], P["tsd"]], P["W1"].ravel(), P["b1"], P["W2"].ravel(),
                            P["b2"], P["w3"], [P["b3"]]])
-    g = np_grad(unpack(flat, F, H), X.astype(np.float64), T.astype(np.float64))
+    g = np_grad(unpack(flat, F, H), X.astype(np.float64), T.astype(np.float64), fw)
     h = 1e-6
     fd = np.zeros_like(g)
     for q in range(2 * F + 2, len(flat)):
         a, b = flat.copy(), flat.copy()
         a[q] += h
         b[q] -= h
-        fd[q] = (np_loss(unpack(a, F, H), X, T) - np_loss(unpack(b, F, H), X, T)) / (2 * h)
+        fd[q] = (np_loss(unpack(a, F, H), X, T, fw) - np_loss(unpack(b, F, H), X, T, fw)) / (2 * h)
     assert np.allclose(g, fd, rtol=1e-5, atol=1e-7 * np.abs(g).max())
 
 
@@ -47,3 +50,11 @@ def test_forward_matches_a_loop_over_one_sample():
     w3 = flat[o2 + H:o2 + 2 * H]
     ys = flat[-1] + sum(w3[k] * h2[k] for k in range(H))
     assert abs(y[s] - ys) <= 1e-12 * max(1.0, abs(ys))
+
+
+def test_weights_favour_fast_samples_and_average_one():
+    from _mlp_ref import np_weights
+    t = np.array([-2.0, 0.0, 1.5])
+    w = np_weights(t, 1.0)
+    assert abs(w.mean() - 1.0) < 1e-12 and w[0] > w[1] > w[2]
+    assert np.allclose(w[0] / w[1], np.exp(2.0)) and np.allclose(np_weights(t, 0.0), 1.0)
