@@ -175,3 +175,49 @@ def study(n_variants: int = 512, n_train: int | None = None, n: int = 256, seed:
         "mlp_pick_shape": [*pm["block"], pm["flags"]],
         "best_all_index": int(vs[int(np.argmin(all_ms))]["index"]),
     }
+
+
+def run_variant(index: int, n: int = 256, reps: int = 10, seed: int = inputs.SEED_VARIANTS,
+                scope: int = binding.SCOPE_MARCH) -> dict:
+    """Generate, compile and run one variant `reps` times on the n^3 RHS workload (through
+    acs_rhs_saturated for a march variant); returns its mean CUDA-event time."""
+    import torch
+    src, _, info = binding.acs_variant_generate(seed, index, scope)
+    v = binding.Variant(src, info)
+    U = torch.from_numpy(inputs.rhs_field(n, halo=2, seed=inputs.SEED_RHS_LARGE)).cuda()
+    R = torch.empty((5, n, n, n), dtype=torch.float64, device="cuda")
+    fn = (lambda: binding.acs_rhs_saturated(U, R, variant=v)) if scope == binding.SCOPE_MARCH else \
+        (lambda: v.launch(U, R))
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    b.synchronize()
+    out = {"index": index, "grid": n, "ms": a.elapsed_time(b) / reps, "regs": v.regs, "block": list(v.block),
+           "flags": v.flags}
+    v.close()
+    return out
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+
+    from . import build as acs_build
+    ap = argparse.ArgumentParser(description="rewriter variants: the ranker study, or one variant's run")
+    ap.add_argument("what", choices=["study", "run"])
+    ap.add_argument("--index", type=int, default=0, help="run: the variant index")
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--variants", type=int, default=512)
+    ap.add_argument("--reps", type=int, default=10)
+    ap.add_argument("--scope", default="march", choices=["march", "iteration"])
+    a = ap.parse_args()
+    acs_build.build()
+    sc = binding.SCOPE_MARCH if a.scope == "march" else binding.SCOPE_ITERATION
+    if a.what == "run":
+        print(json.dumps(run_variant(a.index, a.n, a.reps, scope=sc)))
+    else:
+        print(json.dumps(study(n_variants=a.variants, n=a.n, scope=sc)))
