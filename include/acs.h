@@ -44,7 +44,8 @@
  *    human-readable reason for the last failure of the calling thread.
  *  - Inputs and outputs must not overlap in memory (ACS_ERR_ALIAS).
  *  - The saturated RHS computes 1/rho with a refined hardware reciprocal estimate for
- *    normal rho in [2^-1000, 2^1000] and falls back to an IEEE division otherwise.
+ *    normal |rho| in [2^-1000, 2^1001), faithful (within 1 ulp of the correctly rounded 1/rho),
+ *    and falls back to an IEEE division otherwise.
  */
 #ifndef ACS_H
 #define ACS_H
