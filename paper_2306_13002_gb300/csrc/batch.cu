@@ -58,8 +58,13 @@ __device__ __forceinline__ int find_item(const long long* __restrict__ prefix, i
     return lo;
 }
 
+// The star stencil stages planes two steps ahead here (StarShape DEPTH 2): small grids give
+// many edge tiles whose few active warps cannot hide one plane's copy latency per step.
+constexpr int kBatchStarDepth = 2;
+
 template <int BX, int BY, int KIND>
-__global__ void __launch_bounds__(BX * BY, KIND == ACS_KIND_RHS ? RhsShape<BX, BY>::MINB : StarShape<BX, BY>::MINB)
+__global__ void __launch_bounds__(BX * BY, KIND == ACS_KIND_RHS ? RhsShape<BX, BY>::MINB
+                                                                 : StarShape<BX, BY, kBatchStarDepth>::MINB)
     batch_kernel(const unsigned char* __restrict__ ws, unsigned long long* counter, RhsConst rk, StarCoef sc) {
     extern __shared__ __align__(128) double smem[];
     __shared__ long long s_unit;
@@ -87,14 +92,15 @@ __global__ void __launch_bounds__(BX * BY, KIND == ACS_KIND_RHS ? RhsShape<BX, B
         if (KIND == ACS_KIND_RHS)
             rhs_march<BX, BY, false>(d.in0, d.out, d.g, rk, tx * BX, ty * BY, k0, k1, smem, nullptr, nullptr);
         else
-            star_march<BX, BY, false>(d.in0, d.in1, d.out, d.g, sc, tx * BX, ty * BY, k0, k1, smem, nullptr, nullptr);
+            star_march<BX, BY, false, kBatchStarDepth>(d.in0, d.in1, d.out, d.g, sc, tx * BX, ty * BY, k0, k1, smem,
+                                                        nullptr, nullptr);
     }
 }
 
 template <int BX, int BY, int KIND>
 acs_status launch_batch_t(const BatchPlanHost& p, unsigned long long* counter, const RhsConst& rk,
                           const StarCoef& sc, cudaStream_t s) {
-    const size_t smem = KIND == ACS_KIND_RHS ? RhsShape<BX, BY>::BYTES : StarShape<BX, BY>::BYTES;
+    const size_t smem = KIND == ACS_KIND_RHS ? RhsShape<BX, BY>::BYTES : StarShape<BX, BY, kBatchStarDepth>::BYTES;
     const void* fn = (const void*)batch_kernel<BX, BY, KIND>;
     acs_status st = ensure_smem(fn, smem);
     if (st != ACS_OK) return st;
@@ -106,6 +112,19 @@ acs_status launch_batch_t(const BatchPlanHost& p, unsigned long long* counter, c
     if (blocks > p.total) blocks = p.total;
     batch_kernel<BX, BY, KIND><<<(unsigned)blocks, dim3(BX, BY, 1), smem, s>>>(p.ws, counter, rk, sc);
     return launch_status("batch_kernel");
+}
+
+// Blocks of the batch kernel resident on the whole device at once (0 if the query fails).
+template <int BX, int BY, int KIND>
+long long resident_t() {
+    const size_t smem = KIND == ACS_KIND_RHS ? RhsShape<BX, BY>::BYTES : StarShape<BX, BY, kBatchStarDepth>::BYTES;
+    if (ensure_smem((const void*)batch_kernel<BX, BY, KIND>, smem) != ACS_OK) return 0;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<BX, BY, KIND>, BX * BY, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return (long long)per_sm * num_sms();
 }
 
 template <int KIND>
@@ -126,8 +145,32 @@ acs_status dispatch(const BatchPlanHost& p, unsigned long long* counter, const R
         if (bx == 64 && by == 4) return launch_batch_t<64, 4, KIND>(p, counter, rk, sc, s);
         if (bx == 64 && by == 8) return launch_batch_t<64, 8, KIND>(p, counter, rk, sc, s);
         if (bx == 16 && by == 16) return launch_batch_t<16, 16, KIND>(p, counter, rk, sc, s);
+        if (bx == 16 && by == 8) return launch_batch_t<16, 8, KIND>(p, counter, rk, sc, s);
     }
     return fail(ACS_ERR_UNSUPPORTED, "batch tile %dx%d is not built", bx, by);
+}
+
+long long resident_batch_blocks(int kind, const acs_tile& t) {
+    long long r = 0;
+    const int bx = t.bx, by = t.by;
+    if (kind == ACS_KIND_RHS) {
+        if (bx == 32 && by == 8) r = resident_t<32, 8, ACS_KIND_RHS>();
+        if (bx == 32 && by == 4) r = resident_t<32, 4, ACS_KIND_RHS>();
+        if (bx == 32 && by == 16) r = resident_t<32, 16, ACS_KIND_RHS>();
+        if (bx == 16 && by == 8) r = resident_t<16, 8, ACS_KIND_RHS>();
+        if (bx == 16 && by == 16) r = resident_t<16, 16, ACS_KIND_RHS>();
+        if (bx == 64 && by == 4) r = resident_t<64, 4, ACS_KIND_RHS>();
+    } else {
+        if (bx == 32 && by == 8) r = resident_t<32, 8, ACS_KIND_STENCIL>();
+        if (bx == 32 && by == 4) r = resident_t<32, 4, ACS_KIND_STENCIL>();
+        if (bx == 32 && by == 16) r = resident_t<32, 16, ACS_KIND_STENCIL>();
+        if (bx == 64 && by == 4) r = resident_t<64, 4, ACS_KIND_STENCIL>();
+        if (bx == 64 && by == 8) r = resident_t<64, 8, ACS_KIND_STENCIL>();
+        if (bx == 16 && by == 16) r = resident_t<16, 16, ACS_KIND_STENCIL>();
+        if (bx == 16 && by == 8) r = resident_t<16, 8, ACS_KIND_STENCIL>();
+    }
+    // unknown (no device, or an unbuilt tile rejected later): the former estimate
+    return r > 0 ? r : (long long)num_sms() * (kind == ACS_KIND_RHS ? 2 : 4);
 }
 
 }  // namespace
@@ -142,9 +185,9 @@ acs_status batch_pack(const acs_batch_item* items, const Geom* geo, int n, int k
     auto points = [&](int q) { return (long long)geo[q].nx * geo[q].ny * geo[q].nz; };
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return points(x) > points(y); });
     // Guided z-chunks: the grids at the end of the order, whose units make up the last two
-    // waves of the queue (two units per resident block, estimated), take z-chunks a quarter
-    // as long, so the blocks run out of work closer together.
-    const long long waves = 2LL * num_sms() * (kind == ACS_KIND_RHS ? 2 : 4);
+    // waves of the queue (two units per resident block), take z-chunks a quarter as long, so
+    // the blocks run out of work closer together.
+    const long long waves = 2LL * resident_batch_blocks(kind, tile);
     const int tail_kchunk = std::max(1, tile.kchunk / 4);
     std::vector<int> kchunk(n, tile.kchunk);
     std::vector<long long> units(n);

@@ -272,18 +272,29 @@ __device__ __forceinline__ void rhs_march(const double* __restrict__ U, double* 
     }
 }
 
-template <int BX, int BY>
+// DEPTH 1 (the single-grid kernels): a ring of 10 planes, kk-4 .. kk+5, the prologue stages
+// all nine planes the first step's register queue needs through it and each step stages one
+// plane ahead. DEPTH 2 (the batch kernel: small grids give many edge tiles whose few active
+// warps hide neither a plane's copy latency per step nor the prologue): a compact ring of 7
+// planes, kk .. kk+6, two planes staged ahead; the queue's four planes below the chunk are
+// read from global memory in the prologue. The smaller ring lets more blocks share an SM.
+template <int BX, int BY, int DEPTH = 1>
 struct StarShape {
     static constexpr int PX = BX + 8, PY = BY + 8, PLANE = PX * PY;
-    static constexpr int NSLOT = 10;
+    static constexpr int NSLOT = DEPTH == 1 ? 10 : 7;
     static constexpr int CONST_ELEMS = 16;   // staged StarCoef
     // Ring, staged constants, one mbarrier per slot (TMA staging), and 128 bytes to round the
     // ring's base up to a 128-byte boundary.
     static constexpr size_t BYTES = sizeof(double) * ((size_t)NSLOT * PLANE + CONST_ELEMS + NSLOT) + 128;
     static constexpr int NT = BX * BY;
     // Blocks per SM the launch bounds ask registers for: 2048 threads per SM at most (and the
-    // shared memory allows it for every built tile).
-    static constexpr int MINB = NT >= 512 ? 2 : 4;
+    // shared memory allows it for the 256- and 512-thread tiles). The 16 x 8 tile, added for
+    // batches of small grids (its edge tiles leave fewer idle warps), asks for up to 7 blocks
+    // where its shared memory admits them: 72 registers and no spills (8 blocks at 64 registers
+    // spilled and measured 0.5 % slower on the 64-grid batch); the 32 x 4 tile keeps its measured
+    // bound of 4.
+    static constexpr int FIT = (int)((227u * 1024u) / (BYTES + 1024));
+    static constexpr int MINB = NT >= 512 ? 2 : (NT >= 256 || BX != 16) ? 4 : (FIT < 7 ? FIT : 7);
     static_assert((PLANE * sizeof(double)) % 128 == 0, "every ring slot 128-byte aligned");
 };
 
@@ -310,11 +321,12 @@ __device__ __forceinline__ void load_star_plane(double* slot, const double* __re
 // tensor copy (`map`: the 3D tensor map of u) that completes on the slot's mbarrier, and the
 // readers wait on that mbarrier (bounded; timeouts counted in *tmo). The box of plane q is
 // the q-th plane's fill number n = (q - k0 + 4) / 10 of its slot, so its phase parity is n & 1.
-template <int BX, int BY, bool TMA>
+template <int BX, int BY, bool TMA, int DEPTH = 1>
 __device__ __forceinline__ void star_march(const double* __restrict__ u, const double* __restrict__ a,
                                            double* __restrict__ out, const Geom& g, const StarCoef& cfc, int i0, int j0,
                                            int k0, int k1, double* smem_raw, const CUtensorMap* map, unsigned* tmo) {
-    using S = StarShape<BX, BY>;
+    using S = StarShape<BX, BY, DEPTH>;
+    static_assert(DEPTH == 1 || (DEPTH == 2 && !TMA), "two planes ahead: element-wise staging only");
     constexpr int PX = S::PX, PLANE = S::PLANE;
     constexpr unsigned kPlaneBytes = PLANE * sizeof(double);
     // The ring's base rounded up to 128 bytes (a TMA destination must be). This also measured
@@ -359,10 +371,17 @@ __device__ __forceinline__ void star_march(const double* __restrict__ u, const d
             ok = mbar_wait_bounded(bars + sidx(q), parity(q), tmo);
             if (!ok) lost = q;
         }
-    } else {
+    } else if (DEPTH == 1) {
         for (int q = k0 - 4; q <= k0 + 4; ++q) load_star_plane<BX, BY>(slot(q), u, g, i0, j0, q, tid);
         cp_async_commit();
         cp_async_wait_all();
+    } else {
+        for (int q = k0; q <= k0 + 4; ++q) load_star_plane<BX, BY>(slot(q), u, g, i0, j0, q, tid);
+        cp_async_commit();
+        cp_async_wait_all();
+        // plane k0+5 in its own group, waited for at the end of step k0
+        if (k0 + 5 <= k1 + 3) load_star_plane<BX, BY>(slot(k0 + 5), u, g, i0, j0, k0 + 5, tid);
+        cp_async_commit();
     }
     __syncthreads();
     const StarCoef cf = stage_consts_read<StarCoef>(Cs);   // the weights in registers (see Pipe)
@@ -370,15 +389,25 @@ __device__ __forceinline__ void star_march(const double* __restrict__ u, const d
     // The own column's values at planes kk-4 .. kk+4 live in registers (zq[m] = plane
     // kk-4+m): the z-terms and the centre read no shared memory, and each step reads one new
     // value (plane kk+5, the plane that has just landed). Only the x/y neighbours come from
-    // the ring. (Cells of inactive threads are read but never used.)
+    // the ring. (Cells of inactive threads are read but never used.) With the compact ring the
+    // four planes below the chunk come from global memory (active threads only).
     double zq[9];
+    if (DEPTH == 1) {
 #pragma unroll
-    for (int m = 0; m < 9; ++m) zq[m] = slot(k0 - 4 + m)[own];
+        for (int m = 0; m < 9; ++m) zq[m] = slot(k0 - 4 + m)[own];
+    } else {
+        const double* uc = u + (i64)(k0 - 4 + g.halo) * g.isz + (i64)(j + g.halo) * g.isy + (i + g.halo);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) zq[m] = active ? __ldg(uc + m * g.isz) : 0.0;
+#pragma unroll
+        for (int m = 4; m < 9; ++m) zq[m] = slot(k0 - 4 + m)[own];
+    }
 
     const double* ap = a + (i64)(k0 + g.halo) * g.isz + (i64)(j + g.halo) * g.isy + (i + g.halo);
     for (int kk = k0; kk < k1; ++kk) {
-        // Bulk-load the plane the next step needs into the slot of plane kk-5 (read last in
-        // step kk-5, several barriers ago).
+        // Bulk-load plane kk+4+DEPTH (read first, into the register queue, at the end of step
+        // kk+DEPTH-1) into the slot of plane kk+4+DEPTH-NSLOT: kk-5 (DEPTH 1) or kk-1 (DEPTH 2),
+        // read last in that step, before the barrier that ended it.
         const bool next = kk + 5 <= k1 + 3;
         if (TMA) {
             if (next && tid == 0 && ok) {
@@ -386,7 +415,7 @@ __device__ __forceinline__ void star_march(const double* __restrict__ u, const d
                 issue(kk + 5);
             }
         } else {
-            if (next) load_star_plane<BX, BY>(slot(kk + 5), u, g, i0, j0, kk + 5, tid);
+            if (kk + 4 + DEPTH <= k1 + 3) load_star_plane<BX, BY>(slot(kk + 4 + DEPTH), u, g, i0, j0, kk + 4 + DEPTH, tid);
             cp_async_commit();
         }
         if (active) {
@@ -408,8 +437,10 @@ __device__ __forceinline__ void star_march(const double* __restrict__ u, const d
                 ok = mbar_wait_bounded(bars + sidx(kk + 5), parity(kk + 5), tmo);
                 if (!ok) lost = kk + 5;
             }
-        } else {
+        } else if (DEPTH == 1) {
             cp_async_wait_all();
+        } else {
+            cp_async_wait_group1();   // every group but this step's: plane kk+5 has landed
         }
         __syncthreads();
 #pragma unroll
@@ -423,6 +454,9 @@ __device__ __forceinline__ void star_march(const double* __restrict__ u, const d
         __syncthreads();
         if (tid == 0)
             for (int s = 0; s < S::NSLOT; ++s) mbar_inval(bars + s);
+    } else if (DEPTH == 2) {
+        cp_async_wait_all();   // nothing in flight when the caller reuses the ring
+        __syncthreads();
     }
 }
 

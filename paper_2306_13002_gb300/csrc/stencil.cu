@@ -121,7 +121,7 @@ acs_status launch_star_t(const double* u, const double* a, double* out, const Ge
 
 bool star_tile_supported(int bx, int by) {
     return (bx == 32 && (by == 4 || by == 8 || by == 16)) || (bx == 64 && (by == 4 || by == 8)) ||
-           (bx == 16 && by == 16);
+           (bx == 16 && (by == 8 || by == 16));
 }
 
 size_t star_smem_bytes(int bx, int by) {
@@ -131,6 +131,7 @@ size_t star_smem_bytes(int bx, int by) {
     if (bx == 64 && by == 4) return StarShape<64, 4>::BYTES;
     if (bx == 64 && by == 8) return StarShape<64, 8>::BYTES;
     if (bx == 16 && by == 16) return StarShape<16, 16>::BYTES;
+    if (bx == 16 && by == 8) return StarShape<16, 8>::BYTES;
     return 0;
 }
 
@@ -150,6 +151,7 @@ acs_status launch_stencil_saturated(const double* u, const double* a, double* ou
     if (t.bx == 64 && t.by == 4) return launch_star_t<64, 4>(u, a, out, g, c, t.kchunk, t.flags, s);
     if (t.bx == 64 && t.by == 8) return launch_star_t<64, 8>(u, a, out, g, c, t.kchunk, t.flags, s);
     if (t.bx == 16 && t.by == 16) return launch_star_t<16, 16>(u, a, out, g, c, t.kchunk, t.flags, s);
+    if (t.bx == 16 && t.by == 8) return launch_star_t<16, 8>(u, a, out, g, c, t.kchunk, t.flags, s);
     return fail(ACS_ERR_UNSUPPORTED, "stencil tile %dx%d is not built", t.bx, t.by);
 }
 

@@ -41,7 +41,9 @@ std::string key_of(int kind, const Geom* g, int n) {
 }
 
 const int kRhsTiles[][2] = {{32, 8}, {32, 4}, {32, 16}, {16, 8}, {16, 16}, {64, 4}};
-const int kStarTiles[][2] = {{32, 8}, {32, 4}, {32, 16}, {64, 4}, {64, 8}, {16, 16}};
+const int kStarTiles[][2] = {{32, 8}, {32, 4}, {32, 16}, {64, 4}, {64, 8}, {16, 16}, {16, 8}};
+constexpr int kNumRhsTiles = (int)(sizeof(kRhsTiles) / sizeof(kRhsTiles[0]));
+constexpr int kNumStarTiles = (int)(sizeof(kStarTiles) / sizeof(kStarTiles[0]));
 // z-chunk candidates; kBalanced stands for the balanced schedule (ACS_TILE_BALANCED).
 constexpr int kBalanced = -1;
 const int kChunks[] = {8, 16, 32, 64, kBalanced};
@@ -157,7 +159,7 @@ acs_status tune_rhs(const double* U, double* R, const Geom& g, const RhsConst& k
                     float* best_ms) {
     static const int staging[] = {0, ACS_TILE_TMA};   // element-wise cp.async or TMA plane copies
     return tune_grid(
-        ACS_KIND_RHS, g, kRhsTiles, 6, staging, 2,
+        ACS_KIND_RHS, g, kRhsTiles, kNumRhsTiles, staging, 2,
         [&](const acs_tile& c) { return launch_rhs_saturated(U, R, g, k, c, s); }, s, best, best_ms);
 }
 
@@ -165,7 +167,7 @@ acs_status tune_stencil(const double* u, const double* a, double* out, const Geo
                         cudaStream_t s, acs_tile* best, float* best_ms) {
     static const int staging[] = {0, ACS_TILE_TMA};   // element-wise cp.async or TMA plane copies
     return tune_grid(
-        ACS_KIND_STENCIL, g, kStarTiles, 6, staging, 2,
+        ACS_KIND_STENCIL, g, kStarTiles, kNumStarTiles, staging, 2,
         [&](const acs_tile& c) { return launch_stencil_saturated(u, a, out, g, cf, c, s); }, s, best, best_ms);
 }
 
@@ -175,10 +177,11 @@ acs_status tune_batch(const acs_batch_item* items, const Geom* geo, int n, int k
     Timer t;
     if (!t.init()) return launch_status("cudaEventCreate");
     const int(*tiles)[2] = kind == ACS_KIND_RHS ? kRhsTiles : kStarTiles;
+    const int ntiles = kind == ACS_KIND_RHS ? kNumRhsTiles : kNumStarTiles;
     acs_tile bt = {0, 0, 0, 0};
     float bms = 1e30f;
-    static const int chunks[] = {4, 8, 16, 32};
-    for (int q = 0; q < 6; ++q) {
+    static const int chunks[] = {4, 6, 8, 12, 16, 32};
+    for (int q = 0; q < ntiles; ++q) {
         for (int kc : chunks) {
             acs_tile cand = {tiles[q][0], tiles[q][1], kc, 0};
             BatchPlanHost plan;
