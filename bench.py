@@ -422,9 +422,11 @@ def bench_block(torch, binding, inputs, stream, steps: int) -> dict:
     return res
 
 
-def bench_batch(torch, binding, inputs, stream, steps: int) -> dict:
+def bench_batch(torch, binding, inputs, stream, steps: int, tile=None) -> dict:
     """64 star-stencil grids, sides log-uniform in [16, 160]: per-grid launches vs one
-    persistent batch launch vs the autotuned batch replayed from a CUDA graph."""
+    persistent batch launch vs the autotuned batch replayed from a CUDA graph (`tile`: use this
+    shape for both batch legs instead of the default and the autotuner's)."""
+    given = tile is not None
     sides = inputs.batch_sides(64, seed=inputs.SEED_BATCH)
     grids = []
     for q, (nx, ny, nz) in enumerate(sides):
@@ -439,7 +441,7 @@ def bench_batch(torch, binding, inputs, stream, steps: int) -> dict:
         for (u, a, out) in grids:
             binding.acs_stencil_saturated(u, a, out, stream=stream)
 
-    plan = binding.acs_batch_prepare(binding.KIND_STENCIL, grids, ws, stream=stream)
+    plan = binding.acs_batch_prepare(binding.KIND_STENCIL, grids, ws, tile=tile, stream=stream)
     batch = lambda: binding.acs_batch_launch(plan, stream=stream)  # noqa: E731
     for name, fn in (("per_grid_launches", per_grid), ("batch_launch", batch)):
         for _ in range(3):
@@ -447,7 +449,8 @@ def bench_batch(torch, binding, inputs, stream, steps: int) -> dict:
         torch.cuda.synchronize()
         _, rm = time_launches(torch, fn, steps, stream)
         res[name] = {"ms": rm / steps, "gpts": points / (rm / steps * 1e-3) / 1e9}
-    tile, _ = binding.acs_autotune_batch(binding.KIND_STENCIL, grids, ws, stream=stream)
+    if tile is None:
+        tile, _ = binding.acs_autotune_batch(binding.KIND_STENCIL, grids, ws, stream=stream)
     plan_t = binding.acs_batch_prepare(binding.KIND_STENCIL, grids, ws, tile=tile, stream=stream)
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
@@ -462,7 +465,8 @@ def bench_batch(torch, binding, inputs, stream, steps: int) -> dict:
         graph.replay()
     torch.cuda.synchronize()
     _, rm = time_launches(torch, graph.replay, steps, stream)
-    res["graph_autotuned"] = {"ms": rm / steps, "gpts": points / (rm / steps * 1e-3) / 1e9, "tile": list(tile)}
+    res["graph_autotuned"] = {"ms": rm / steps, "gpts": points / (rm / steps * 1e-3) / 1e9, "tile": list(tile),
+                              "tile_source": "given" if given else "acs_autotune_batch"}
     return res
 
 
@@ -601,7 +605,8 @@ def main() -> None:
         from paper_2306_13002_gb300 import build as acs_build
         acs_build.build()
         stream = torch.cuda.current_stream()
-        res = bench_batch(torch, binding, inputs, stream, max(3, min(args.steps, 50)))
+        tile = tuple(int(v) for v in args.tile.split(",")) if args.tile else None
+        res = bench_batch(torch, binding, inputs, stream, max(3, min(args.steps, 50)), tile=tile)
         print(json.dumps({"workload": "star_stencil_batch_64_grids_fp64", "unit": "ms per batch", **res}))
         return
     if args.ranker:
