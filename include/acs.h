@@ -128,11 +128,13 @@ typedef struct acs_tile {
 #define ACS_TILE_BALANCED 1
 /* acs_tile.flags: stage each xy-plane of the input into shared memory with one tensor copy
  * (TMA, cp.async.bulk.tensor) completing on an mbarrier, instead of element-wise cp.async.
- * Accepted by the single-grid saturated calls and their autotuners (the batch entry points
- * reject it). Used where the layout allows it (16-byte aligned input, row, plane and component
- * strides that are multiples of 2 elements, even halo); other layouts are staged element-wise,
- * with the same results. Waits on the mbarriers are bounded (about one second); one that runs out
- * is counted (acs_wait_timeouts) and the call's results are then wrong, but the kernel ends. */
+ * Accepted by the single-grid saturated calls, their autotuners and star-stencil batches
+ * (acs_batch_prepare, acs_autotune_batch: per grid; RHS batches and acs_batch_run_static reject
+ * it). Used where the layout allows it (16-byte aligned input, row, plane and component strides
+ * that are multiples of 2 elements, even halo); other layouts, or other grids of a batch, are
+ * staged element-wise, with the same results. Waits on the mbarriers are bounded (about one
+ * second); one that runs out is counted (acs_wait_timeouts) and the call's results are then
+ * wrong, but the kernel ends. */
 #define ACS_TILE_TMA 2
 
 /*
@@ -256,7 +258,9 @@ size_t acs_batch_workspace_bytes(int n);
  * would, including the alias check), order them largest first, and upload the unit table
  * into `ws` (16-byte aligned device memory of at least acs_batch_workspace_bytes(n) bytes:
  * ACS_ERR_ALIGN / ACS_ERR_WORKSPACE otherwise). `tile` NULL = 32 x 8 with z-chunks of 16
- * planes. On success fills `plan`.
+ * planes; tile->flags may be ACS_TILE_TMA for a star-stencil batch, which encodes a tensor map
+ * per grid into the workspace (grids of even row and plane pitch are then staged by tensor
+ * copies, the others element-wise). On success fills `plan`.
  */
 acs_status acs_batch_prepare(const acs_batch_item *items, int n, int kind, const acs_tile *tile, void *ws,
                              size_t ws_bytes, acs_batch_plan *plan, acs_stream stream);
@@ -373,6 +377,7 @@ acs_status acs_variant_build(const char *src, const acs_variant_info *info, acs_
  * runs with its own tile and flags (as acs_rhs_saturated with tile NULL). */
 acs_status acs_variant_launch(acs_variant_handle h, const double *U, double *R, const acs_grid *g,
                               const acs_rhs_params *p, acs_stream stream);
+/* Unload a variant; call it only after every launch of the variant has completed. */
 void acs_variant_free(acs_variant_handle h);
 
 /* FP32 MLP ranker (3 layers, ReLU, hidden width `hidden`): parameters and workspace sizes. */

@@ -512,7 +512,10 @@ acs_status acs_batch_prepare(const acs_batch_item* items, int n, int kind, const
         return fail(ACS_ERR_WORKSPACE, "workspace %zu bytes < %zu needed for %d grids", ws_bytes, batch_ws_bytes(n), n);
     acs_tile t = tile ? *tile : acs_tile{32, 8, 16, 0};
     if (t.kchunk == 0) t.kchunk = 16;
-    if (t.flags != 0 || t.kchunk < 1) return fail(ACS_ERR_INVALID, "bad batch tile (kchunk %d, flags %d)", t.kchunk, t.flags);
+    if ((t.flags & ~ACS_TILE_TMA) != 0 || t.kchunk < 1)
+        return fail(ACS_ERR_INVALID, "bad batch tile (kchunk %d, flags %d)", t.kchunk, t.flags);
+    if ((t.flags & ACS_TILE_TMA) && kind != ACS_KIND_STENCIL)
+        return fail(ACS_ERR_UNSUPPORTED, "TMA staging in a batch is built for the star stencil only");
     if (!(kind == ACS_KIND_RHS ? rhs_tile_supported(t.bx, t.by) : star_tile_supported(t.bx, t.by)))
         return fail(ACS_ERR_UNSUPPORTED, "tile %dx%d is not built", t.bx, t.by);
     BatchPlanHost hp;

@@ -12,6 +12,10 @@
 //   [0, 64)                BatchHeader (the work counter, the unit total, the shape)
 //   [64, 64 + n*D)         BatchDesc per grid, in processing order
 //   [.., + 8 (n+1))        prefix sums of the grids' unit counts
+//   [maps, + 128 n)        star-stencil batches with ACS_TILE_TMA: a tensor map per grid, in
+//                          processing order, at the first 128-byte aligned address after the
+//                          prefix sums (the header records the offset); grids whose layout TMA
+//                          cannot copy are staged element-wise.
 // acs_batch_prepare uploads everything but the counter; acs_batch_launch zeroes the
 // counter with a memset on the stream and launches, so a prepared batch can be launched
 // repeatedly and captured in a CUDA graph (a memset node plus a kernel node).
@@ -30,12 +34,14 @@ struct BatchDesc {
     double* out;
     Geom g;
     int ntx, nty, nkc, kchunk;   // this grid's z-chunk (see batch_pack)
+    int tma, pad;                // tma: this grid's planes are staged by its tensor map
 };
+static_assert(sizeof(BatchDesc) <= 112, "the static batch scratch is sized for 112-byte descriptors");
 
 struct BatchHeader {
     unsigned long long counter;
     long long total;
-    int n, kind, bx, by, kchunk, pad0;
+    int n, kind, bx, by, kchunk, maps_off;   // maps_off: byte offset of the tensor maps (0: none)
     long long pad1[3];
 };
 static_assert(sizeof(BatchHeader) == 64, "batch header is 64 bytes");
@@ -65,7 +71,8 @@ constexpr int kBatchStarDepth = 2;
 template <int BX, int BY, int KIND>
 __global__ void __launch_bounds__(BX * BY, KIND == ACS_KIND_RHS ? RhsShape<BX, BY>::MINB
                                                                  : StarShape<BX, BY, kBatchStarDepth>::MINB)
-    batch_kernel(const unsigned char* __restrict__ ws, unsigned long long* counter, RhsConst rk, StarCoef sc) {
+    batch_kernel(const unsigned char* __restrict__ ws, unsigned long long* counter, RhsConst rk, StarCoef sc,
+                 unsigned* tmo) {
     extern __shared__ __align__(128) double smem[];
     __shared__ long long s_unit;
     const BatchHeader* h = reinterpret_cast<const BatchHeader*>(ws);
@@ -89,11 +96,17 @@ __global__ void __launch_bounds__(BX * BY, KIND == ACS_KIND_RHS ? RhsShape<BX, B
         const int kc = (int)(lu / d.nty);
         const int k0 = kc * d.kchunk;
         const int k1 = min(k0 + d.kchunk, d.g.nz);
-        if (KIND == ACS_KIND_RHS)
+        if (KIND == ACS_KIND_RHS) {
             rhs_march<BX, BY, false>(d.in0, d.out, d.g, rk, tx * BX, ty * BY, k0, k1, smem, nullptr, nullptr);
-        else
+        } else if (d.tma) {
+            const CUtensorMap* map = reinterpret_cast<const CUtensorMap*>(ws + h->maps_off) + it;
+            if (leader) tensormap_acquire(map);
+            star_march<BX, BY, true, kBatchStarDepth>(d.in0, d.in1, d.out, d.g, sc, tx * BX, ty * BY, k0, k1, smem,
+                                                       map, tmo);
+        } else {
             star_march<BX, BY, false, kBatchStarDepth>(d.in0, d.in1, d.out, d.g, sc, tx * BX, ty * BY, k0, k1, smem,
                                                         nullptr, nullptr);
+        }
     }
 }
 
@@ -110,7 +123,9 @@ acs_status launch_batch_t(const BatchPlanHost& p, unsigned long long* counter, c
     if (per_sm < 1) return fail(ACS_ERR_UNSUPPORTED, "batch kernel %dx%d does not fit on an SM", BX, BY);
     long long blocks = (long long)per_sm * num_sms();
     if (blocks > p.total) blocks = p.total;
-    batch_kernel<BX, BY, KIND><<<(unsigned)blocks, dim3(BX, BY, 1), smem, s>>>(p.ws, counter, rk, sc);
+    unsigned* tmo = wait_timeout_counter();
+    if (!tmo) return fail(ACS_ERR_CUDA, "cannot address the wait-timeout counter");
+    batch_kernel<BX, BY, KIND><<<(unsigned)blocks, dim3(BX, BY, 1), smem, s>>>(p.ws, counter, rk, sc, tmo);
     return launch_status("batch_kernel");
 }
 
@@ -175,11 +190,14 @@ long long resident_batch_blocks(int kind, const acs_tile& t) {
 
 }  // namespace
 
-size_t batch_ws_bytes(int n) { return n < 1 ? 0 : kHeader + desc_bytes(n) + sizeof(long long) * (size_t)(n + 1); }
+// Header, descriptors and prefix sums; the tensor maps follow at a 128-byte aligned address.
+static size_t batch_table_bytes(int n) { return kHeader + desc_bytes(n) + sizeof(long long) * (size_t)(n + 1); }
+
+size_t batch_ws_bytes(int n) { return n < 1 ? 0 : batch_table_bytes(n) + 128 + sizeof(CUtensorMap) * (size_t)n; }
 
 // Host half of acs_batch_prepare: geometry already validated; builds the packed image.
 acs_status batch_pack(const acs_batch_item* items, const Geom* geo, int n, int kind, const acs_tile& tile,
-                      std::vector<unsigned char>& image, long long& total) {
+                      uintptr_t ws_addr, std::vector<unsigned char>& image, long long& total) {
     std::vector<int> order(n);
     std::iota(order.begin(), order.end(), 0);
     auto points = [&](int q) { return (long long)geo[q].nx * geo[q].ny * geo[q].nz; };
@@ -214,6 +232,13 @@ acs_status batch_pack(const acs_batch_item* items, const Geom* geo, int n, int k
     h.kchunk = tile.kchunk;
     BatchDesc* d = reinterpret_cast<BatchDesc*>(image.data() + kHeader);
     long long* prefix = reinterpret_cast<long long*>(image.data() + kHeader + desc_bytes(n));
+    // Tensor maps of a star-stencil batch staged by TMA: at the first 128-byte aligned device
+    // address after the table.
+    const bool tma = (tile.flags & ACS_TILE_TMA) && kind == ACS_KIND_STENCIL;
+    if (tma) {
+        const uintptr_t first = (ws_addr + batch_table_bytes(n) + 127) & ~(uintptr_t)127;
+        h.maps_off = (int)(first - ws_addr);
+    }
     long long acc = 0;
     for (int r = 0; r < n; ++r) {
         const int q = order[r];
@@ -228,6 +253,16 @@ acs_status batch_pack(const acs_batch_item* items, const Geom* geo, int n, int k
         e.nty = (g.ny + tile.by - 1) / tile.by;
         e.nkc = (g.nz + kchunk[q] - 1) / kchunk[q];
         e.kchunk = kchunk[q];
+        if (tma) {   // a layout TMA cannot copy (odd pitch, misaligned base) is staged element-wise
+            CUtensorMap map;
+            std::memset(&map, 0, sizeof(map));
+            if (encode_plane_map(items[q].in0, g, 1, tile.bx + 8, tile.by + 8, &map) == ACS_OK) {
+                e.tma = 1;
+                std::memcpy(image.data() + h.maps_off + (size_t)r * sizeof(CUtensorMap), &map, sizeof(map));
+            } else {
+                set_error("%s", "");
+            }
+        }
         d[r] = e;
         prefix[r] = acc;
         acc += units[q];
@@ -243,7 +278,7 @@ acs_status batch_prepare_host(const acs_batch_item* items, const Geom* geo, int 
                               unsigned char* ws, size_t ws_bytes, cudaStream_t s, BatchPlanHost& plan) {
     std::vector<unsigned char> image;
     long long total = 0;
-    acs_status st = batch_pack(items, geo, n, kind, tile, image, total);
+    acs_status st = batch_pack(items, geo, n, kind, tile, (uintptr_t)ws, image, total);
     if (st != ACS_OK) return st;
     if (image.size() > ws_bytes) return fail(ACS_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, image.size());
     if (cudaMemcpyAsync(ws, image.data(), image.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)

@@ -29,8 +29,11 @@ namespace {
 
 constexpr int kStaticMaxGrids = ACS_BATCH_STATIC_MAX;
 
-// Sized for the largest batch accepted (checked against batch_ws_bytes at set-up).
-constexpr size_t kStaticBytes = 64 + 112 * (size_t)kStaticMaxGrids + 8 * (size_t)(kStaticMaxGrids + 1) + 256;
+// Sized for the largest batch accepted (checked against batch_ws_bytes on every call): header,
+// 112-byte descriptors, prefix sums and the tensor-map area of the workspace layout (unused
+// here: these calls stage element-wise), about 64 KB.
+constexpr size_t kStaticBytes =
+    64 + 112 * (size_t)kStaticMaxGrids + 8 * (size_t)(kStaticMaxGrids + 1) + 256 + 128 * (size_t)(kStaticMaxGrids + 1);
 
 static __device__ __align__(256) unsigned char g_batch_scratch[kStaticBytes];
 

@@ -326,7 +326,7 @@ __device__ __forceinline__ void star_march(const double* __restrict__ u, const d
                                            double* __restrict__ out, const Geom& g, const StarCoef& cfc, int i0, int j0,
                                            int k0, int k1, double* smem_raw, const CUtensorMap* map, unsigned* tmo) {
     using S = StarShape<BX, BY, DEPTH>;
-    static_assert(DEPTH == 1 || (DEPTH == 2 && !TMA), "two planes ahead: element-wise staging only");
+    static_assert(DEPTH == 1 || DEPTH == 2, "one or two planes ahead");
     constexpr int PX = S::PX, PLANE = S::PLANE;
     constexpr unsigned kPlaneBytes = PLANE * sizeof(double);
     // The ring's base rounded up to 128 bytes (a TMA destination must be). This also measured
@@ -349,11 +349,14 @@ __device__ __forceinline__ void star_march(const double* __restrict__ u, const d
     double* Cs = smem + S::NSLOT * PLANE;
     uint64_t* bars = reinterpret_cast<uint64_t*>(Cs + S::CONST_ELEMS);
     static_assert(sizeof(StarCoef) <= S::CONST_ELEMS * sizeof(double), "constant staging area");
-    auto parity = [&](int q) -> unsigned { return (unsigned)((q - k0 + 4) / S::NSLOT) & 1u; };
+    // Fill number of plane q's slot: planes are issued in order from k0-4 (DEPTH 1) or k0 (DEPTH 2).
+    auto parity = [&](int q) -> unsigned { return (unsigned)((q - k0 + (DEPTH == 1 ? 4 : 0)) / S::NSLOT) & 1u; };
+    int last_issued = 0;                     // thread 0: the last plane copied (DEPTH 2)
     auto issue = [&](int q) {   // thread 0 only
         uint64_t* bar = bars + sidx(q);
         mbar_arrive_expect_tx(bar, kPlaneBytes);
         tma_load_3d(slot(q), map, bar, i0 - 4 + g.halo, j0 - 4 + g.halo, q + g.halo);
+        last_issued = q;
     };
     bool ok = true;                          // this thread's waits have all completed
     int lost = 0x7fffffff;                   // thread 0: the plane whose wait ran out
@@ -365,9 +368,12 @@ __device__ __forceinline__ void star_march(const double* __restrict__ u, const d
             fence_mbar_init();
         }
         __syncthreads();
-        if (tid == 0)
-            for (int q = k0 - 4; q <= k0 + 4; ++q) issue(q);
-        for (int q = k0 - 4; q <= k0 + 4 && ok; ++q) {
+        const int qlo = DEPTH == 1 ? k0 - 4 : k0;
+        if (tid == 0) {
+            for (int q = qlo; q <= k0 + 4; ++q) issue(q);
+            if (DEPTH == 2 && k0 + 5 <= k1 + 3) issue(k0 + 5);   // waited for at the end of step k0
+        }
+        for (int q = qlo; q <= k0 + 4 && ok; ++q) {
             ok = mbar_wait_bounded(bars + sidx(q), parity(q), tmo);
             if (!ok) lost = q;
         }
@@ -410,9 +416,9 @@ __device__ __forceinline__ void star_march(const double* __restrict__ u, const d
         // read last in that step, before the barrier that ended it.
         const bool next = kk + 5 <= k1 + 3;
         if (TMA) {
-            if (next && tid == 0 && ok) {
+            if (kk + 4 + DEPTH <= k1 + 3 && tid == 0 && ok) {
                 fence_proxy_async();
-                issue(kk + 5);
+                issue(kk + 4 + DEPTH);
             }
         } else {
             if (kk + 4 + DEPTH <= k1 + 3) load_star_plane<BX, BY>(slot(kk + 4 + DEPTH), u, g, i0, j0, kk + 4 + DEPTH, tid);
@@ -449,8 +455,13 @@ __device__ __forceinline__ void star_march(const double* __restrict__ u, const d
     }
     if (TMA) {
         // A copy whose wait ran out may still be in flight: give it one more bounded wait
-        // before the slots are reused or the block exits. Then retire the barriers.
-        if (tid == 0 && !ok && lost != 0x7fffffff) mbar_wait_bounded(bars + sidx(lost), parity(lost), tmo);
+        // before the slots are reused or the block exits (two planes ahead, also the copies
+        // issued after it). Then retire the barriers.
+        if (tid == 0 && !ok && lost != 0x7fffffff) {
+            mbar_wait_bounded(bars + sidx(lost), parity(lost), tmo);
+            if (DEPTH == 2)
+                for (int q = lost + 1; q <= last_issued; ++q) mbar_wait_bounded(bars + sidx(q), parity(q), tmo);
+        }
         __syncthreads();
         if (tid == 0)
             for (int s = 0; s < S::NSLOT; ++s) mbar_inval(bars + s);
@@ -458,6 +469,13 @@ __device__ __forceinline__ void star_march(const double* __restrict__ u, const d
         cp_async_wait_all();   // nothing in flight when the caller reuses the ring
         __syncthreads();
     }
+}
+
+// Makes a tensor map that the host wrote to global memory before the launch visible to the
+// tensor-copy proxy of this thread (PTX fence.proxy.tensormap, acquire, GPU scope).
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap* map) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+                 : "memory");
 }
 
 }  // namespace acs

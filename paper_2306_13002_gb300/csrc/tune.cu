@@ -181,9 +181,12 @@ acs_status tune_batch(const acs_batch_item* items, const Geom* geo, int n, int k
     acs_tile bt = {0, 0, 0, 0};
     float bms = 1e30f;
     static const int chunks[] = {4, 6, 8, 12, 16, 32};
+    // star-stencil batches also try TMA plane staging (used for the grids whose layout allows it)
+    const int nstaging = kind == ACS_KIND_STENCIL ? 2 : 1;
     for (int q = 0; q < ntiles; ++q) {
         for (int kc : chunks) {
-            acs_tile cand = {tiles[q][0], tiles[q][1], kc, 0};
+          for (int f = 0; f < nstaging; ++f) {
+            acs_tile cand = {tiles[q][0], tiles[q][1], kc, f ? ACS_TILE_TMA : 0};
             BatchPlanHost plan;
             acs_status st = batch_prepare_host(items, geo, n, kind, cand, ws, ws_bytes, s, plan);
             if (st != ACS_OK) return st;
@@ -194,6 +197,7 @@ acs_status tune_batch(const acs_batch_item* items, const Geom* geo, int n, int k
                 bms = ms;
                 bt = cand;
             }
+          }
         }
     }
     {

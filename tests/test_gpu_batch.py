@@ -214,3 +214,70 @@ def test_autotune_batch_picks_a_working_tile():
     for (u, a), (_, _, out) in zip(host, grids):
         assert_parity(out.cpu().numpy(), oracle.stencil(u, a), what=f"tuned batch {u.shape}")
     binding.acs_tune_cache_clear()
+
+
+def _padded(arr, pitch):
+    """Device view of `arr` whose rows sit in a buffer of row pitch `pitch` (elements)."""
+    v = inputs.pad_rows(arr, pitch)
+    return torch.from_numpy(v.base).cuda()[..., :arr.shape[-1]]
+
+
+@pytest.mark.parametrize("tile", [(16, 8, 8, binding.TILE_TMA), (32, 8, 16, binding.TILE_TMA),
+                                  (16, 16, 4, binding.TILE_TMA)])
+def test_stencil_batch_tma_mixed_layouts(tile):
+    """A star-stencil batch with TMA staging: grids of even row pitch are copied by tensor
+    copies, the odd-pitch ones element-wise, a padded one (odd side, even pitch) by tensor
+    copies; every grid matches the oracle, its halo is untouched and no bounded wait ran out.
+    The same plan replayed from a CUDA graph gives the same bits."""
+    sides = [(40, 17, 9), (33, 70, 12), (64, 8, 30), (20, 20, 20), (5, 3, 2), (16, 24, 7), (31, 9, 15)]
+    grids, host = [], []
+    for q, (nx, ny, nz) in enumerate(sides):
+        u, a = inputs.stencil_fields(nx, ny, nz, halo=4, seed=7400 + q)
+        out = torch.full((nz + 2, ny, nx), float("nan"), dtype=torch.float64, device="cuda")
+        if q == len(sides) - 1:                     # odd side, rows padded to an even pitch
+            ud, ad = _padded(u, nx + 9), _padded(a, nx + 9)
+        else:
+            ud, ad = to_dev(u), to_dev(a)
+        grids.append((ud, ad, out[1:-1]))
+        host.append((u, a, out))
+    plan = binding.acs_batch_prepare(binding.KIND_STENCIL, grids, _ws(len(grids)), tile=tile)
+    binding.acs_batch_launch(plan)
+    torch.cuda.synchronize()
+    first = []
+    for (u, a, out) in host:
+        o = out.cpu().numpy()
+        assert np.isnan(o[0]).all() and np.isnan(o[-1]).all()
+        assert_parity(o[1:-1], oracle.stencil(u, a), what=f"TMA batch {tile} grid {u.shape}")
+        first.append(o.copy())
+    assert binding.acs_wait_timeouts() == 0
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        binding.acs_batch_launch(plan, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        binding.acs_batch_launch(plan, stream=torch.cuda.current_stream())
+    for (_, _, out) in host:
+        out[1:-1].fill_(float("nan"))
+    graph.replay()
+    torch.cuda.synchronize()
+    for (_, _, out), o in zip(host, first):
+        assert np.array_equal(out.cpu().numpy()[1:-1], o[1:-1])
+    assert binding.acs_wait_timeouts() == 0
+
+
+def test_batch_tma_flag_rules():
+    sides = [(8, 8, 4)]
+    grids, _ = _stencil_batch(sides, 7500)
+    U = to_dev(inputs.rhs_field(8, 8, 4, halo=2, seed=7501))
+    R = torch.empty((5, 4, 8, 8), dtype=torch.float64, device="cuda")
+    with pytest.raises(binding.AcsError) as ei:            # RHS batches stage element-wise only
+        binding.acs_batch_prepare(binding.KIND_RHS, [(U, None, R)], _ws(1), tile=(32, 8, 8, binding.TILE_TMA))
+    assert ei.value.name == "ACS_ERR_UNSUPPORTED"
+    with pytest.raises(binding.AcsError) as ei:            # balanced has no meaning in a batch
+        binding.acs_batch_prepare(binding.KIND_STENCIL, grids, _ws(1), tile=(32, 8, 8, binding.TILE_BALANCED))
+    assert ei.value.name == "ACS_ERR_INVALID"
+    with pytest.raises(binding.AcsError):                  # the static entry point stages element-wise
+        binding.acs_batch_run_static(binding.KIND_STENCIL, grids, tile=(32, 8, 8, binding.TILE_TMA))
