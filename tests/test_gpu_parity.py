@@ -179,18 +179,33 @@ def test_rhs_scaled_fields(form, scale_exp):
 @pytest.mark.parametrize("rho_exp", [-1010, -990, 990, 1010])
 def test_rhs_saturated_reciprocal_range(rho_exp):
     """rho = 2^e * base, m = 2^(e/2) * base (so |m|^2/rho stays O(1)): at |e| = 1010 the
-    saturated reciprocal takes its IEEE-division fallback, at |e| = 990 the refined
-    estimate. Components have very different scales here, so each is compared relative to
-    its own largest magnitude."""
-    U = inputs.rhs_field(13, 10, 9, halo=2, seed=3200)
+    saturated reciprocal takes its IEEE-division fallback, at |e| = 990 the refined estimate.
+    The components' magnitudes then span about 2^+-500, so the fixed 1e-14 floor means nothing
+    here; instead every point of every component is compared with its exact value (rational
+    evaluation, oracle/exact.py): |R - exact| <= 1e-12 |exact| + 2^-46 sum|terms|, where
+    sum|terms| is the point's condition scale (every addend of the as-written sums) and 2^-46
+    covers the roundings any order of those ~40 additions can incur (each at most 2^-53 of the
+    scale). The FP64 oracle meets the same bound."""
+    from oracle import exact
+    nx, ny, nz = 7, 6, 5
+    U = inputs.rhs_field(nx, ny, nz, halo=2, seed=3200)
     U[0] *= 2.0 ** rho_exp
     U[1:4] *= 2.0 ** (rho_exp // 2)
     ref = oracle.rhs(U)
     R = _rhs_gpu("saturated", U).cpu().numpy()
-    assert np.isfinite(ref).all()
-    for c in range(5):
-        scale = np.max(np.abs(ref[c]))
-        assert_parity(R[c] / scale, ref[c] / scale, what=f"rhs saturated rho 2^{rho_exp} comp {c}")
+    assert np.isfinite(ref).all() and np.isfinite(R).all()
+    worst = 0.0
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                ex, sc = exact.rhs_point(U, i, j, k, gamma=1.4, eps=0.25, halo=2)
+                for c in range(5):
+                    e = float(ex[c])
+                    tol = 1e-12 * abs(e) + 2.0 ** -46 * float(sc[c])
+                    assert abs(R[c, k, j, i] - e) <= tol, (rho_exp, c, k, j, i, R[c, k, j, i], e, tol)
+                    assert abs(ref[c, k, j, i] - e) <= tol, ("oracle", rho_exp, c, k, j, i)
+                    worst = max(worst, abs(R[c, k, j, i] - e) / tol)
+    assert worst <= 1.0
 
 
 def test_rhs_constant_dyadic_field_is_zero():

@@ -245,3 +245,28 @@ def test_model_save_and_load_round_trip(tmp_path):
     assert binding.acs_variant_rank(Xd, q, hidden=H) == binding.acs_variant_rank(Xd, p, hidden=H)
     small = torch.empty(q.numel() - 1, dtype=torch.float32, device="cuda")
     assert binding.lib().acs_ranker_load(str(path).encode(), small.data_ptr(), small.numel(), None, None) == 8
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (17, 1, 3), (2, 40, 1), (16, 16, 2), (33, 9, 1)])
+def test_march_variants_on_degenerate_grids(shape, march_variants):
+    """One of each staging x schedule among the bench's march variants, on grids of one plane,
+    one row, one point: within the parity tolerance of the oracle (element-wise staged variants
+    also where the pitch is odd; TMA variants where the layout allows them)."""
+    nx, ny, nz = shape
+    U = inputs.rhs_field(nx, ny, nz, halo=2, seed=8400 + nx + 7 * ny + 31 * nz)
+    ref = oracle.rhs(U)
+    Ud = to_dev(U)
+    seen = set()
+    for v in march_variants:
+        key = v["flags"]
+        if key in seen:
+            continue
+        if (v["flags"] & binding.TILE_TMA) and (nx + 4) % 2:
+            continue                                  # odd pitch: TMA variants refuse it
+        seen.add(key)
+        R = torch.full((5, nz, ny, nx), float("nan"), dtype=torch.float64, device="cuda")
+        binding.acs_rhs_saturated(Ud, R, variant=v["module"])
+        torch.cuda.synchronize()
+        assert_parity(R.cpu().numpy(), ref, what=f"march variant {v['index']} on {shape}")
+    assert len(seen) >= (2 if (nx + 4) % 2 else 4)
+    assert binding.acs_wait_timeouts() == 0

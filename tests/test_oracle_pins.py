@@ -289,3 +289,22 @@ def test_stencil_padding_and_slabs_bitwise(orc):
 def test_openmp_threads_do_not_change_bits(orc):
     U = inputs.rhs_field(8, halo=2, seed=81)
     np.testing.assert_array_equal(orc.rhs(U, threads=1), orc.rhs(U, threads=4))
+
+
+@pytest.mark.parametrize("rho_exp", [-1010, 1010])
+def test_oracle_extreme_density_within_condition_bound_of_exact(rho_exp):
+    """rho scaled by 2^+-1010 (momenta by 2^+-505): at every point the FP64 oracle is within
+    1e-12 |exact| + 2^-46 sum|terms| of the exact rational value, the per-point bound the GPU
+    test of these fields uses."""
+    from oracle import exact
+    U = inputs.rhs_field(5, 4, 3, halo=2, seed=3200)
+    U[0] *= 2.0 ** rho_exp
+    U[1:4] *= 2.0 ** (rho_exp // 2)
+    ref = oracle.rhs(U)
+    for k in range(3):
+        for j in range(4):
+            for i in range(5):
+                ex, sc = exact.rhs_point(U, i, j, k, gamma=1.4, eps=0.25, halo=2)
+                for c in range(5):
+                    e = float(ex[c])
+                    assert abs(ref[c, k, j, i] - e) <= 1e-12 * abs(e) + 2.0 ** -46 * float(sc[c])
