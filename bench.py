@@ -388,6 +388,38 @@ def fp64_probe(torch, binding, stream, sms: int, sampler, blocks_per_sm: int = 2
             "blocks_per_sm": blocks_per_sm, "threads": threads, "ops_per_launch": ops, "launch_ms": launch_ms}
 
 
+def host_link_floor(torch, U_pin, U, R, R_pin, stream, reps: int) -> dict:
+    """The host link under the end-to-end step, measured on the same pinned buffers: the upload of
+    U alone, the download of R alone, and both at once on two streams (the floor of a step that
+    moves both, whatever the overlap with the kernel)."""
+    side = torch.cuda.Stream()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    def both():
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            R_pin.copy_(R, non_blocking=True)
+        U.copy_(U_pin, non_blocking=True)
+        stream.wait_stream(side)
+
+    up = timed(lambda: U.copy_(U_pin, non_blocking=True))
+    down = timed(lambda: R_pin.copy_(R, non_blocking=True))
+    bi = timed(both)
+    nu, nd = U.numel() * 8, R.numel() * 8
+    return {"upload_ms": up, "download_ms": down, "both_ms": bi, "upload_gbs": nu / (up * 1e-3) / 1e9,
+            "download_gbs": nd / (down * 1e-3) / 1e9, "both_gbs": (nu + nd) / (bi * 1e-3) / 1e9}
+
+
 def time_launches(torch, fn, steps: int, stream) -> tuple[float, float]:
     """Per-launch CUDA-event durations on `stream`; returns (mean launch ms, region ms)."""
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -764,7 +796,8 @@ def run_ours(args) -> None:
         _, ser_region = time_launches(torch, serial_step, e2e_steps, stream)
         e2e = {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_ms, "h2d_bytes_per_step": in_bytes,
                "d2h_bytes_per_step": out_bytes, "entry_point": "acs_rhs_saturated_host (pinned host U, R)",
-               "serial_copy_kernel_copy_ms": ser_region / e2e_steps}
+               "serial_copy_kernel_copy_ms": ser_region / e2e_steps,
+               "host_link": host_link_floor(torch, U_pin, U, R, R_pin, stream, max(3, min(args.steps, 10)))}
         del ws_e2e
 
     # Star stencil, both forms, as context (one replica per rank, rank 0 reports).

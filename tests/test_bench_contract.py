@@ -49,3 +49,7 @@ def test_default_arm_line():
     assert d["clocks"]["samples"] >= 10 and d["clocks"]["sm_mhz"] > 0
     e = d["e2e"]
     assert e["value"] > 0 and e["h2d_bytes_per_step"] == 703040000 and e["d2h_bytes_per_step"] == 671088640
+    # the host link measured under the step: moving both directions at once is its floor
+    link = e["host_link"]
+    assert 0 < link["both_ms"] <= e["ms_per_step"] * 1.02
+    assert link["upload_gbs"] > 50 and link["download_gbs"] > 50
