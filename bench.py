@@ -420,8 +420,9 @@ def host_link_floor(torch, U_pin, U, R, R_pin, stream, reps: int) -> dict:
             "download_gbs": nd / (down * 1e-3) / 1e9, "both_gbs": (nu + nd) / (bi * 1e-3) / 1e9}
 
 
-def time_launches(torch, fn, steps: int, stream) -> tuple[float, float]:
-    """Per-launch CUDA-event durations on `stream`; returns (mean launch ms, region ms)."""
+def time_launches(torch, fn, steps: int, stream, per=None) -> tuple[float, float]:
+    """Per-launch CUDA-event durations on `stream`; returns (mean launch ms, region ms) and
+    appends every launch's duration to `per` if given."""
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -432,8 +433,10 @@ def time_launches(torch, fn, steps: int, stream) -> tuple[float, float]:
         ends[s].record(stream)
     r1.record(stream)
     torch.cuda.synchronize()
-    per = [a.elapsed_time(b) for a, b in zip(starts, ends)]
-    return sum(per) / len(per), r0.elapsed_time(r1)
+    durations = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    if per is not None:
+        per.extend(durations)
+    return sum(durations) / len(durations), r0.elapsed_time(r1)
 
 
 def bench_block(torch, binding, inputs, stream, steps: int) -> dict:
@@ -784,7 +787,17 @@ def run_ours(args) -> None:
         e2e_step()
         sync()
         e2e_steps = max(3, min(args.steps, 20))
-        e2e_ms, e2e_value = timed(e2e_step, e2e_steps)
+        per_step = []
+
+        def step_timer(fn, steps):       # the region on CUDA events, and each step's own time
+            mean, region = time_launches(torch, fn, steps, stream, per_step)
+            return region
+
+        ta = time.time()
+        e2e_region = timed_replica_region(dist, e2e_step, e2e_steps, step_timer, sync)
+        if sampler:
+            sampler.window(ta, time.time())
+        e2e_ms, e2e_value, _ = replica_throughput(dist, e2e_region, e2e_steps, points, "cuda")
 
         def serial_step():   # for comparison: upload, kernel, download in sequence on one stream
             U.copy_(U_pin, non_blocking=True)
@@ -796,6 +809,8 @@ def run_ours(args) -> None:
         _, ser_region = time_launches(torch, serial_step, e2e_steps, stream)
         e2e = {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_ms, "h2d_bytes_per_step": in_bytes,
                "d2h_bytes_per_step": out_bytes, "entry_point": "acs_rhs_saturated_host (pinned host U, R)",
+               "step_ms_median": statistics.median(per_step), "step_ms_min": min(per_step),
+               "step_ms_max": max(per_step),
                "serial_copy_kernel_copy_ms": ser_region / e2e_steps,
                "host_link": host_link_floor(torch, U_pin, U, R, R_pin, stream, max(3, min(args.steps, 10)))}
         del ws_e2e
