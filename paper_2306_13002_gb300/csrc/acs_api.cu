@@ -305,6 +305,7 @@ acs_status rhs_const(const acs_rhs_params* p, RhsConst& k) {
     k.hz2i = 0.5 / p->h[2];
     k.neps = -p->eps;
     k.pp = Pipe{1.0, -1.0, -0.0};
+    k.nhg1s = k.nhg1 / k.sx;
     return ACS_OK;
 }
 

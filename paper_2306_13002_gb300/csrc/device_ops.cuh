@@ -76,7 +76,7 @@ __device__ __forceinline__ double psub(double a, double b, const Pipe& p) { retu
 __device__ __forceinline__ double pmul(double a, double b, const Pipe& p) { return fma(a, b, p.nz); }
 
 // RHS constants folded on the host (Table I constant folding):
-//   g1 = gamma - 1, nhg1 = -(gamma - 1)/2, s_d = -1/(2 h_d), neps = -eps.
+//   g1 = gamma - 1, nhg1 = -(gamma - 1)/2, s_d = -1/(2 h_d), neps = -eps, nhg1s = nhg1 / s_x.
 // The as-written form uses half_h_inv[d] = 1/(2 h_d) as a loop-invariant factor.
 struct RhsConst {
     double gamma, eps;
@@ -85,6 +85,7 @@ struct RhsConst {
     double hx2i, hy2i, hz2i;       // +1/(2h) per axis (as-written form)
     double neps;
     Pipe pp;
+    double nhg1s;                  // nhg1 / sx, for the isotropic saturated form (sx = sy = sz)
 };
 
 // Stencil weights: c[d][o-1] and the folded centre weight C0 = -2 sum c.

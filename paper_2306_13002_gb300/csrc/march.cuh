@@ -14,7 +14,7 @@ struct RhsShape {
     static constexpr int U_ELEMS = NSLOT * 5 * PLANE;
     static constexpr int FX_ELEMS = 4 * BY * (BX + 2);
     static constexpr int FY_ELEMS = 4 * (BY + 2) * BX;
-    static constexpr int CONST_ELEMS = 16;   // staged constants (RhsRegs)
+    static constexpr int CONST_ELEMS = 18;   // staged constants (RhsRegs)
     // U ring, flux planes, staged constants, one mbarrier per slot (TMA staging).
     static constexpr size_t BYTES = sizeof(double) * (size_t)(U_ELEMS + FX_ELEMS + FY_ELEMS + CONST_ELEMS + NSLOT);
     static constexpr int NT = BX * BY;
@@ -33,27 +33,38 @@ struct RhsRegs {
 // The 12 non-trivial flux values of one point (component 0 of F_d is m_d itself).
 // fx = F_x[1..4], fy = F_y[1..4], fz = F_z[1..4]. Every caller uses this one definition,
 // so a flux value is bit-identical whichever thread computes it.
+//
+// ISO (isotropic spacing, s = s_x = s_y = s_z = -1/(2h)): the fluxes come out already scaled
+// by s, which then need not multiply their differences. s enters once through the reciprocal
+// (v' = m (s/rho) = s v, so every product m_c v'_d and (E + P) v'_d is s times the flux term)
+// and once through P (P' = s P, added to the diagonal); the pressure itself uses
+// sum m v' = s |m|^2/rho with the folded constant nhg1 / s. Two more operations per point,
+// four fewer per point in the combine (one per flux component). Distributivity and constant
+// folding: the same value up to rounding.
+template <bool ISO = false>
 __device__ __forceinline__ void point_flux(double rho, double mx, double my, double mz, double E, const RhsConst& k,
                                            double fx[4], double fy[4], double fz[4]) {
     const Pipe& q = k.pp;
-    const double r = rcp_refined(rho, q.one);
+    const double r0 = rcp_refined(rho, q.one);
+    const double r = ISO ? pmul(r0, k.sx, q) : r0;
     const double vx = pmul(mx, r, q), vy = pmul(my, r, q), vz = pmul(mz, r, q);
     const double mxvx = pmul(mx, vx, q);
     const double twoKE = fma(mz, vz, fma(my, vy, mxvx));
-    const double P = fma(k.nhg1, twoKE, pmul(k.g1, E, q));
+    const double P = fma(ISO ? k.nhg1s : k.nhg1, twoKE, pmul(k.g1, E, q));
+    const double Pd = ISO ? pmul(P, k.sx, q) : P;   // the pressure term of the diagonal fluxes
     const double EP = padd(E, P, q);
     const double oxy = pmul(mx, vy, q), oxz = pmul(mx, vz, q), oyz = pmul(my, vz, q);
-    fx[0] = padd(mxvx, P, q);
+    fx[0] = padd(mxvx, Pd, q);
     fx[1] = oxy;
     fx[2] = oxz;
     fx[3] = pmul(EP, vx, q);
     fy[0] = oxy;
-    fy[1] = fma(my, vy, P);
+    fy[1] = fma(my, vy, Pd);
     fy[2] = oyz;
     fy[3] = pmul(EP, vy, q);
     fz[0] = oxz;
     fz[1] = oyz;
-    fz[2] = fma(mz, vz, P);
+    fz[2] = fma(mz, vz, Pd);
     fz[3] = pmul(EP, vz, q);
 }
 
@@ -86,7 +97,7 @@ __device__ __forceinline__ void load_plane(double* slot, const double* __restric
 // plane q with one tensor copy (`map`: the 4D tensor map of U, components outermost) that
 // completes on the slot's mbarrier, and the readers wait on it (bounded; timeouts counted in
 // *tmo). Plane q is fill number n = (q - k0 + 2) / 5 of its slot: phase parity n & 1.
-template <int BX, int BY, bool TMA>
+template <int BX, int BY, bool TMA, bool ISO = false>
 __device__ __forceinline__ void rhs_march(const double* __restrict__ U, double* __restrict__ R, const Geom& g,
                                           const RhsConst& kc, int i0, int j0, int k0, int k1, double* smem,
                                           const CUtensorMap* map, unsigned* tmo) {
@@ -162,9 +173,9 @@ __device__ __forceinline__ void rhs_march(const double* __restrict__ U, double* 
     if (fluxer) {
         const double* s = slot(k0 - 1);
         double ux[4], uy[4];
-        point_flux(s[own], s[PLANE + own], s[2 * PLANE + own], s[3 * PLANE + own], s[4 * PLANE + own], k, ux, uy, fzm);
+        point_flux<ISO>(s[own], s[PLANE + own], s[2 * PLANE + own], s[3 * PLANE + own], s[4 * PLANE + own], k, ux, uy, fzm);
         s = slot(k0);
-        point_flux(s[own], s[PLANE + own], s[2 * PLANE + own], s[3 * PLANE + own], s[4 * PLANE + own], k, pfx, pfy, fz0);
+        point_flux<ISO>(s[own], s[PLANE + own], s[2 * PLANE + own], s[3 * PLANE + own], s[4 * PLANE + own], k, pfx, pfy, fz0);
     }
 
     for (int kk = k0; kk < k1; ++kk) {
@@ -184,7 +195,7 @@ __device__ __forceinline__ void rhs_march(const double* __restrict__ U, double* 
             const int rx = tid >> 1, ry = (tid & 1) ? BY : -1;
             const int e = (ry + 2) * PX + (rx + 2);
             double fx[4], fy[4], fz[4];
-            point_flux(s0[e], s0[PLANE + e], s0[2 * PLANE + e], s0[3 * PLANE + e], s0[4 * PLANE + e], k, fx, fy, fz);
+            point_flux<ISO>(s0[e], s0[PLANE + e], s0[2 * PLANE + e], s0[3 * PLANE + e], s0[4 * PLANE + e], k, fx, fy, fz);
 #pragma unroll
             for (int c = 0; c < 4; ++c) Fys[(c * (BY + 2) + ry + 1) * BX + rx] = fy[c];
         } else if (tid < 2 * (BX + BY)) {
@@ -192,14 +203,14 @@ __device__ __forceinline__ void rhs_march(const double* __restrict__ U, double* 
             const int ry = t >> 1, rx = (t & 1) ? BX : -1;
             const int e = (ry + 2) * PX + (rx + 2);
             double fx[4], fy[4], fz[4];
-            point_flux(s0[e], s0[PLANE + e], s0[2 * PLANE + e], s0[3 * PLANE + e], s0[4 * PLANE + e], k, fx, fy, fz);
+            point_flux<ISO>(s0[e], s0[PLANE + e], s0[2 * PLANE + e], s0[3 * PLANE + e], s0[4 * PLANE + e], k, fx, fy, fz);
 #pragma unroll
             for (int c = 0; c < 4; ++c) Fxs[(c * BY + ry) * (BX + 2) + rx + 1] = fx[c];
         }
         // (2) all fluxes of the own point at plane kk+1.
         if (fluxer) {
             const double* s = slot(kk + 1);
-            point_flux(s[own], s[PLANE + own], s[2 * PLANE + own], s[3 * PLANE + own], s[4 * PLANE + own], k, pfx, pfy,
+            point_flux<ISO>(s[own], s[PLANE + own], s[2 * PLANE + own], s[3 * PLANE + own], s[4 * PLANE + own], k, pfx, pfy,
                        fzp);
         }
         if (TMA)
@@ -219,20 +230,27 @@ __device__ __forceinline__ void rhs_march(const double* __restrict__ U, double* 
 #pragma unroll
             for (int c = 0; c < 5; ++c) {
                 const int cb = c * PLANE + own;
-                double fxd, fyd, fzd;
+                double fl;
                 if (c == 0) {
-                    fxd = psub(s0[PLANE + own + 1], s0[PLANE + own - 1], q);
-                    fyd = psub(s0[2 * PLANE + own + PX], s0[2 * PLANE + own - PX], q);
-                    fzd = psub(sp1[3 * PLANE + own], sm1[3 * PLANE + own], q);
+                    const double fxd = psub(s0[PLANE + own + 1], s0[PLANE + own - 1], q);
+                    const double fyd = psub(s0[2 * PLANE + own + PX], s0[2 * PLANE + own - PX], q);
+                    const double fzd = psub(sp1[3 * PLANE + own], sm1[3 * PLANE + own], q);
+                    fl = pmul(fxd, k.sx, q);
+                    fl = fma(fyd, k.sy, fl);
+                    fl = fma(fzd, k.sz, fl);
                 } else {
                     const double* fxr = Fxs + ((c - 1) * BY + ty) * (BX + 2) + tx;
-                    fxd = psub(fxr[2], fxr[0], q);
-                    fyd = psub(Fys[((c - 1) * (BY + 2) + ty + 2) * BX + tx], Fys[((c - 1) * (BY + 2) + ty) * BX + tx], q);
-                    fzd = psub(fzp[c - 1], fzm[c - 1], q);
+                    const double fyp = Fys[((c - 1) * (BY + 2) + ty + 2) * BX + tx];
+                    const double fym = Fys[((c - 1) * (BY + 2) + ty) * BX + tx];
+                    if (ISO) {   // the fluxes carry s already: sum the three differences
+                        fl = padd(psub(fxr[2], fxr[0], q), psub(fyp, fym, q), q);
+                        fl = padd(fl, psub(fzp[c - 1], fzm[c - 1], q), q);
+                    } else {
+                        fl = pmul(psub(fxr[2], fxr[0], q), k.sx, q);
+                        fl = fma(psub(fyp, fym, q), k.sy, fl);
+                        fl = fma(psub(fzp[c - 1], fzm[c - 1], q), k.sz, fl);
+                    }
                 }
-                double fl = pmul(fxd, k.sx, q);
-                fl = fma(fyd, k.sy, fl);
-                fl = fma(fzd, k.sz, fl);
                 const double s2 = padd(padd(padd(s0[cb - 2], s0[cb + 2], q), padd(s0[cb - 2 * PX], s0[cb + 2 * PX], q), q),
                                        padd(sm2[cb], sp2[cb], q), q);
                 const double s1 = padd(padd(padd(s0[cb - 1], s0[cb + 1], q), padd(s0[cb - PX], s0[cb + PX], q), q),

@@ -11,6 +11,10 @@
 //    neighbours that difference this point's flux read it instead of recomputing it:
 //    x- and y-fluxes through shared memory, z-fluxes through a three-deep register queue
 //    as the block marches along z.
+//  * Equal spacing (h_x = h_y = h_z): the common scale s = -1/(2h) is folded into the fluxes
+//    where they are formed (DISTRIB-MUL, constant folding), so the flux differences of the
+//    momentum and energy components are summed without a multiply: 114 FP64 operations per
+//    point against 116 with three scales.
 //  * Reassociated dissipation (ASSOC-ADD, COMM-ADD, FMA1): the three axes' 5-point fourth
 //    differences become  S2 - 4 S1 + 18 U(p)  with S2 the sum of the six values at
 //    distance 2 and S1 the six at distance 1; combined with the flux sum by one FMA with
@@ -37,14 +41,14 @@
 namespace acs {
 namespace {
 
-template <int BX, int BY, bool TMA>
+template <int BX, int BY, bool TMA, bool ISO>
 __global__ void __launch_bounds__(BX * BY, RhsShape<BX, BY>::MINB)
     rhs_saturated_kernel(const double* __restrict__ U, double* __restrict__ R, Geom g, RhsConst k, int kchunk,
                          const __grid_constant__ CUtensorMap map, unsigned* tmo) {
     extern __shared__ __align__(128) double smem[];
     const int k0 = blockIdx.z * kchunk;
-    rhs_march<BX, BY, TMA>(U, R, g, k, blockIdx.x * BX, blockIdx.y * BY, k0, min(k0 + kchunk, g.nz), smem, &map,
-                           tmo);
+    rhs_march<BX, BY, TMA, ISO>(U, R, g, k, blockIdx.x * BX, blockIdx.y * BY, k0, min(k0 + kchunk, g.nz), smem,
+                                &map, tmo);
 }
 
 // Balanced schedule (ACS_TILE_BALANCED): one block per resident slot, marching the segments
@@ -55,25 +59,25 @@ __global__ void __launch_bounds__(BX * BY, RhsShape<BX, BY>::MINB)
 // z, so the halo planes they share are read from L2: 1.2x the input from DRAM at 256^3,
 // against 2x for the plain contiguous split of the (column, plane) list, which also ran
 // 0.1-1.9 % slower.
-template <int BX, int BY, bool TMA>
+template <int BX, int BY, bool TMA, bool ISO>
 __global__ void __launch_bounds__(BX * BY, RhsShape<BX, BY>::MINB)
     rhs_saturated_balanced_kernel(const double* __restrict__ U, double* __restrict__ R, Geom g, RhsConst k,
                                   BalancedPlan plan, const __grid_constant__ CUtensorMap map, unsigned* tmo) {
     extern __shared__ __align__(128) double smem[];
     balanced_segments(plan, blockIdx.x, [&](i64 col, int z0, int z1) {
-        rhs_march<BX, BY, TMA>(U, R, g, k, (int)(col % plan.ntx) * BX, (int)(col / plan.ntx) * BY, z0, z1, smem,
+        rhs_march<BX, BY, TMA, ISO>(U, R, g, k, (int)(col % plan.ntx) * BX, (int)(col / plan.ntx) * BY, z0, z1, smem,
                                &map, tmo);
     });
 }
 
-template <int BX, int BY, bool TMA>
+template <int BX, int BY, bool TMA, bool ISO>
 acs_status launch_tt(const double* U, double* R, const Geom& g, const RhsConst& k, int kchunk, int flags,
                      const CUtensorMap& map, cudaStream_t s) {
     using S = RhsShape<BX, BY>;
     unsigned* tmo = wait_timeout_counter();
     if (!tmo) return fail(ACS_ERR_CUDA, "cannot address the wait-timeout counter");
     if (flags & ACS_TILE_BALANCED) {
-        const void* fn = (const void*)rhs_saturated_balanced_kernel<BX, BY, TMA>;
+        const void* fn = (const void*)rhs_saturated_balanced_kernel<BX, BY, TMA, ISO>;
         acs_status st = ensure_smem(fn, S::BYTES);
         if (st != ACS_OK) return st;
         const int ntx = (g.nx + BX - 1) / BX;
@@ -82,11 +86,11 @@ acs_status launch_tt(const double* U, double* R, const Geom& g, const RhsConst& 
         if (G <= 0) return fail(ACS_ERR_CUDA, "occupancy query failed for rhs_saturated_balanced_kernel");
         if (G > C * g.nz) G = C * g.nz;
         const BalancedPlan plan = balanced_plan(C, ntx, g.nz, (int)G);
-        rhs_saturated_balanced_kernel<BX, BY, TMA><<<(unsigned)G, dim3(BX, BY, 1), S::BYTES, s>>>(U, R, g, k, plan,
+        rhs_saturated_balanced_kernel<BX, BY, TMA, ISO><<<(unsigned)G, dim3(BX, BY, 1), S::BYTES, s>>>(U, R, g, k, plan,
                                                                                                  map, tmo);
         return launch_status("rhs_saturated_balanced_kernel");
     }
-    const void* fn = (const void*)rhs_saturated_kernel<BX, BY, TMA>;
+    const void* fn = (const void*)rhs_saturated_kernel<BX, BY, TMA, ISO>;
     acs_status st = ensure_smem(fn, S::BYTES);
     if (st != ACS_OK) return st;
     if (kchunk <= 0) {
@@ -95,7 +99,7 @@ acs_status launch_tt(const double* U, double* R, const Geom& g, const RhsConst& 
     }
     dim3 block(BX, BY, 1);
     dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, (g.nz + kchunk - 1) / kchunk);
-    rhs_saturated_kernel<BX, BY, TMA><<<grid, block, S::BYTES, s>>>(U, R, g, k, kchunk, map, tmo);
+    rhs_saturated_kernel<BX, BY, TMA, ISO><<<grid, block, S::BYTES, s>>>(U, R, g, k, kchunk, map, tmo);
     return launch_status("rhs_saturated_kernel");
 }
 
@@ -106,9 +110,13 @@ acs_status launch_t(const double* U, double* R, const Geom& g, const RhsConst& k
     memset(&map, 0, sizeof(map));
     // TMA staging where the layout allows it (the box: the tile plus its 2-cell halo, one
     // plane, all five components of the halo-extended U); element-wise staging otherwise.
+    // Equal spacing on the three axes selects the form with the scale folded into the fluxes.
+    const bool iso = k.sx == k.sy && k.sy == k.sz;
     if ((flags & ACS_TILE_TMA) && encode_plane_map(U, g, 5, BX + 4, BY + 4, &map) == ACS_OK)
-        return launch_tt<BX, BY, true>(U, R, g, k, kchunk, flags, map, s);
-    return launch_tt<BX, BY, false>(U, R, g, k, kchunk, flags, map, s);
+        return iso ? launch_tt<BX, BY, true, true>(U, R, g, k, kchunk, flags, map, s)
+                   : launch_tt<BX, BY, true, false>(U, R, g, k, kchunk, flags, map, s);
+    return iso ? launch_tt<BX, BY, false, true>(U, R, g, k, kchunk, flags, map, s)
+               : launch_tt<BX, BY, false, false>(U, R, g, k, kchunk, flags, map, s);
 }
 
 }  // namespace
