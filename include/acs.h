@@ -169,7 +169,7 @@ acs_status acs_rhs_saturated(const double *U, double *R, const acs_grid *g, cons
 
 /*
  * acs_rhs_saturated_host - the saturated RHS on HOST arrays, streamed through the GPU in
- * z-slabs of `slab` planes (0 = 16) so that uploads, kernels and downloads overlap.
+ * z-slabs of `slab` planes (0 = 12) so that uploads, kernels and downloads overlap.
  *   U, R   host arrays in compact layout (in_sy = nx + 2 halo, in_sz = in_sy (ny + 2 halo),
  *          out_sy = nx, out_sz = nx ny; component strides free). Page-locked memory is
  *          needed for the copies to overlap; pageable memory works but serialises.

@@ -423,7 +423,7 @@ acs_status acs_rhs_saturated(const double* U, double* R, const acs_grid* g, cons
 
 size_t acs_rhs_host_workspace_bytes(const acs_grid* g, int slab) {
     Geom geo;
-    if (slab <= 0) slab = 16;
+    if (slab <= 0) slab = 12;
     if (check_grid(g, 2, 5, geo) != ACS_OK) return 0;
     return rhs_host_ws_bytes(geo, slab < geo.nz ? slab : geo.nz);
 }
@@ -435,7 +435,7 @@ acs_status acs_rhs_saturated_host(const double* U, double* R, const acs_grid* g,
     acs_status st = check_rhs(U, R, g, p, geo, k);
     if (st != ACS_OK) return st;
     if (slab < 0) return fail(ACS_ERR_INVALID, "slab must be >= 0");
-    if (slab == 0) slab = 16;
+    if (slab == 0) slab = 12;
     if (slab > geo.nz) slab = geo.nz;
     acs_tile t;
     st = check_tile(tile, kDefaultRhsTile, rhs_tile_supported, t);
