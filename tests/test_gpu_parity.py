@@ -64,16 +64,18 @@ def test_rhs_saturated_ragged(dims, tile):
     assert_parity(R, ref, what=f"rhs saturated {dims} tile {tile}")
 
 
-@pytest.mark.parametrize("h", [(0.37, 0.37, 0.37), (3.0, 3.0, 3.0), (1.0, 0.5, 2.0), (0.5, 0.5, 0.25),
-                               (2.0 ** -70, 2.0 ** -70, 2.0 ** -70)])
+@pytest.mark.parametrize("h,eps", [((0.37, 0.37, 0.37), 0.25), ((3.0, 3.0, 3.0), 0.25), ((1.0, 0.5, 2.0), 0.25),
+                                   ((0.5, 0.5, 0.25), 0.25), ((2.0 ** -70,) * 3, 0.25 * 2.0 ** 70)])
 @pytest.mark.parametrize("tile", [None, (16, 16, 0, 3), (32, 8, 3, 2), (16, 8, 0, 1), (64, 4, 5, 0)])
-def test_rhs_saturated_spacing(h, tile):
+def test_rhs_saturated_spacing(h, eps, tile):
     """Equal spacing selects the kernel with -1/(2h) folded into the fluxes; unequal spacing, and
     equal spacing outside 2^-65 .. 2^63, keep the three scales. Both against the oracle on a
-    ragged grid, in every staging and schedule."""
+    ragged grid, in every staging and schedule. At h = 2^-70, eps is scaled by 2^70 with the flux
+    term, so that R is exactly 2^70 times an h = 1 result: the per-point rule is relative to |R|,
+    and a flux term 2^70 times the dissipation would judge cancellation, not the kernel."""
     U = inputs.rhs_field(41, 19, 13, halo=2, seed=1700)
-    ref = oracle.rhs(U, h=h, threads=4)
-    R = _rhs_gpu("saturated", U, tile=tile, h=h).cpu().numpy()
+    ref = oracle.rhs(U, eps=eps, h=h, threads=4)
+    R = _rhs_gpu("saturated", U, tile=tile, h=h, eps=eps).cpu().numpy()
     assert_parity(R, ref, what=f"rhs saturated h={h} tile {tile}")
 
 
