@@ -71,12 +71,15 @@ def test_rhs_saturated_spacing(h, eps, tile):
     """Equal spacing selects the kernel with -1/(2h) folded into the fluxes; unequal spacing, and
     equal spacing outside 2^-65 .. 2^63, keep the three scales. Both against the oracle on a
     ragged grid, in every staging and schedule. At h = 2^-70, eps is scaled by 2^70 with the flux
-    term, so that R is exactly 2^70 times an h = 1 result: the per-point rule is relative to |R|,
-    and a flux term 2^70 times the dissipation would judge cancellation, not the kernel."""
+    term, so that R is exactly 2^70 times an h = 1 result, and both sides are compared after the
+    exact division by 2^70: the per-point rule has an absolute floor for points where R cancels,
+    which must scale with R, and a flux term 2^70 times the dissipation would judge cancellation,
+    not the kernel."""
     U = inputs.rhs_field(41, 19, 13, halo=2, seed=1700)
     ref = oracle.rhs(U, eps=eps, h=h, threads=4)
     R = _rhs_gpu("saturated", U, tile=tile, h=h, eps=eps).cpu().numpy()
-    assert_parity(R, ref, what=f"rhs saturated h={h} tile {tile}")
+    sc = eps / 0.25   # a power of two: 1, or 2^70
+    assert_parity(R / sc, ref / sc, what=f"rhs saturated h={h} tile {tile}")
 
 
 @pytest.mark.parametrize("tile", [(16, 16, 0, 3), (32, 8, 0, 3), (64, 4, 2, 0), (32, 4, 0, 1)])
