@@ -114,20 +114,54 @@ def saturated_flux_point(U, i, j, k, gamma):
     }
 
 
-def saturated_rhs_point(U, i, j, k, gamma=1.4, eps=0.25, h=(1.0, 1.0, 1.0), halo=2):
+def scaled_flux_point(U, i, j, k, gamma, s):
+    """The flux set with the common scale s = -1/(2h) of equal spacing folded in where it is
+    formed: r' = s / rho, v' = m r' (= s v), the pressure from sum m v' with the folded
+    constant -(gamma-1) / (2 s), the diagonal fluxes m_d v'_d + s P and the energy fluxes
+    (E + P) v'_d. Components 1..4 come out as s F; component 0 (m_d) is not scaled.
+    """
+    rho = _at(U, 0, i, j, k)
+    mx, my, mz = (_at(U, c, i, j, k) for c in (1, 2, 3))
+    E = _at(U, 4, i, j, k)
+    g1 = Q(float(gamma)) - 1
+    r = (1 / rho) * s
+    vx, vy, vz = mx * r, my * r, mz * r
+    mxvx = mx * vx
+    twoKE = mz * vz + (my * vy + mxvx)
+    P = g1 * E + ((-g1 / 2) / s) * twoKE
+    Pd = P * s
+    EP = E + P
+    mxvy, mxvz, myvz = mx * vy, mx * vz, my * vz
+    return {
+        (0, 0): mx, (0, 1): mxvx + Pd, (0, 2): mxvy, (0, 3): mxvz, (0, 4): EP * vx,
+        (1, 0): my, (1, 1): mxvy, (1, 2): my * vy + Pd, (1, 3): myvz, (1, 4): EP * vy,
+        (2, 0): mz, (2, 1): mxvz, (2, 2): myvz, (2, 3): mz * vz + Pd, (2, 4): EP * vz,
+    }
+
+
+def saturated_rhs_point(U, i, j, k, gamma=1.4, eps=0.25, h=(1.0, 1.0, 1.0), halo=2, scaled=False):
     """R_c via the saturated grouping: flux sum scaled once, dissipation as
-    S2 - 4 S1 + 18 U(p) summed over all three axes, combined last."""
+    S2 - 4 S1 + 18 U(p) summed over all three axes, combined last. With `scaled` (equal
+    spacing only) the fluxes of components 1..4 carry s = -1/(2h) from `scaled_flux_point`
+    and their three differences are summed unscaled."""
     I, J, K = i + halo, j + halo, k + halo
     e = Q(float(eps))
     out = []
     fl = {}
+    if scaled:
+        assert h[0] == h[1] == h[2], "the scaled grouping needs equal spacing"
+        s = -1 / (2 * Q(float(h[0])))
+        point_flux = lambda a, b, c_: scaled_flux_point(U, a, b, c_, gamma, s)  # noqa: E731
+    else:
+        point_flux = lambda a, b, c_: saturated_flux_point(U, a, b, c_, gamma)  # noqa: E731
     for d, ax in enumerate(AXES):
-        fl[(d, +1)] = saturated_flux_point(U, I + ax[0], J + ax[1], K + ax[2], gamma)
-        fl[(d, -1)] = saturated_flux_point(U, I - ax[0], J - ax[1], K - ax[2], gamma)
+        fl[(d, +1)] = point_flux(I + ax[0], J + ax[1], K + ax[2])
+        fl[(d, -1)] = point_flux(I - ax[0], J - ax[1], K - ax[2])
     for c in range(5):
         fsum = Q(0)
         for d in range(3):
-            fsum += (fl[(d, +1)][(d, c)] - fl[(d, -1)][(d, c)]) * (-1 / (2 * Q(float(h[d]))))
+            diff = fl[(d, +1)][(d, c)] - fl[(d, -1)][(d, c)]
+            fsum += diff if (scaled and c > 0) else diff * (-1 / (2 * Q(float(h[d]))))
         s1 = Q(0)
         s2 = Q(0)
         for ax in AXES:

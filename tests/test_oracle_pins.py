@@ -194,6 +194,18 @@ def test_saturated_grouping_is_an_exact_identity(orc):
         assert a == b
 
 
+@pytest.mark.parametrize("h", [1.0, 0.37, 3.0])
+def test_scaled_flux_grouping_is_an_exact_identity(orc, h):
+    """Equal spacing: -1/(2h) folded into the fluxes where they are formed (scaled reciprocal,
+    pressure through the folded constant, scaled diagonal pressure) equals the as-written
+    definition exactly over the rationals."""
+    U = inputs.rhs_field(3, halo=2, seed=81)
+    for (i, j, k) in [(0, 0, 0), (1, 2, 0), (2, 1, 2)]:
+        a, _ = exact.rhs_point(U, i, j, k, h=(h, h, h))
+        b = exact.saturated_rhs_point(U, i, j, k, h=(h, h, h), scaled=True)
+        assert a == b
+
+
 # ----------------------------------------------------------------------------- stencil pins
 
 def test_stencil_constant_is_exact_zero(orc):
