@@ -414,7 +414,8 @@ acs_status acs_variant_rank(const float *feats, int n, int n_feats, const acs_ra
  * then the P parameters in hexadecimal floating point, so a load restores the same bits), and
  * load one back into device memory: params (device) of `capacity` floats, or NULL to read
  * only n_feats / hidden (either may be NULL). ACS_ERR_INVALID for an unreadable or malformed
- * file, ACS_ERR_WORKSPACE if the buffer is too small. Synchronous. */
+ * file, ACS_ERR_WORKSPACE if the buffer is too small. Synchronous: both first wait for all work
+ * on the current device (the model may be written or read on any stream). */
 acs_status acs_ranker_save(const char *path, const acs_ranker_model *model);
 acs_status acs_ranker_load(const char *path, float *params, size_t capacity, int *n_feats, int *hidden);
 

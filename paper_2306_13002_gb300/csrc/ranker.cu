@@ -296,6 +296,9 @@ acs_status ranker_gradient(const float* feats, const float* times, int n, int F,
 acs_status ranker_save(const char* path, const float* params, int F, int H) {
     const Layout L(F, H);
     std::vector<float> p(L.P);
+    // The model may have been trained on any stream (non-blocking ones do not order with this
+    // copy): wait for all work on the device first.
+    if (cudaDeviceSynchronize() != cudaSuccess) return launch_status("ranker_save: waiting for the device");
     if (cudaMemcpy(p.data(), params, L.P * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
         return launch_status("ranker_save: reading the model");
     FILE* f = fopen(path, "w");
@@ -332,6 +335,8 @@ acs_status ranker_load(const char* path, float* params, size_t capacity, int* F_
     if (H_out) *H_out = H;
     if (!params) return ACS_OK;   // size query
     if (capacity < P) return fail(ACS_ERR_WORKSPACE, "model needs %zu floats, buffer holds %zu", P, capacity);
+    // Kernels still reading an earlier model from `params` may run on any stream.
+    if (cudaDeviceSynchronize() != cudaSuccess) return launch_status("ranker_load: waiting for the device");
     if (cudaMemcpy(params, p.data(), P * 4, cudaMemcpyHostToDevice) != cudaSuccess)
         return launch_status("ranker_load: uploading the model");
     return ACS_OK;
