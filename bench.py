@@ -526,7 +526,8 @@ def bench_ranker(binding, ranker, n_variants: int = 512) -> dict:
     ones among `n_variants` rewriter variants (78 % train, the rest ranked by the MLP and by the
     paper's analytical cost), every variant checked against the library's saturated kernel."""
     t = time.time()
-    res = ranker.study(n_variants=n_variants, n=N_RHS, epochs=2000, reps=3, scope=binding.SCOPE_MARCH)
+    res = ranker.study(n_variants=n_variants, n=N_RHS, epochs=2000, reps=3, scope=binding.SCOPE_MARCH,
+                       extra_splits=20)
     res["wall_s"] = time.time() - t
     return res
 
@@ -923,7 +924,9 @@ def run_ours(args) -> None:
         keys = ("variants_generated", "variants_distinct", "train", "test", "fast_weight", "spearman_mlp_test",
                 "spearman_analytical_test", "best_test_ms", "mlp_pick_ms", "analytical_pick_ms", "mlp_pick_over_best",
                 "analytical_pick_over_best", "all_ms_min", "all_ms_median", "all_ms_max",
-                "max_err_over_tol_vs_saturated", "mlp_pick_index", "mlp_pick_shape", "best_all_index", "wall_s")
+                "max_err_over_tol_vs_saturated", "mlp_pick_index", "mlp_pick_shape", "best_all_index",
+                "mlp_top3_measured_over_best", "splits",
+                "wall_s")
         result["ranker"] = {"workload": f"march-scope rewriter variants of the RHS at {N_RHS}^3",
                             **{k: study[k] for k in keys},
                             "builtin_saturated_ms": ms_per_step,
