@@ -298,12 +298,21 @@ def run_reference(args) -> None:
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "rhs_as_written_oracle_256^3_fp64", "grid": [N_RHS] * 3, "halo": 2,
-                   "sample_planes_per_step": planes},
+        "config": workload_config(N_RHS, args.gpus),
+        "form": "as written, the CPU oracle (plain C, FP64, no FMA contraction)",
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"{planes} z-planes of the {N_RHS}^3 field per step ({pts} points)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+def workload_config(n: int, world: int) -> dict:
+    """The workload both arms run (the same dict in the reference arm's line): the RHS of the
+    compressible Euler equations with 4th-order dissipation on an n^3 grid, FP64."""
+    in_b, out_b = 5 * (n + 4) ** 3 * 8, 5 * n ** 3 * 8
+    return {"workload": f"rhs_{n}^3_fp64", "grid": [n] * 3, "halo": 2, "gamma": 1.4, "eps": 0.25,
+            "h": [1.0, 1.0, 1.0], "l2": f"inputs larger than L2 ({in_b / 1e6:.0f} MB in, {out_b / 1e6:.0f} MB out)",
+            "parallelism": f"replicas x{world}"}
 
 
 def reduce_over_ranks(dist, x: float, op: str, device: str) -> float:
@@ -890,9 +899,8 @@ def run_ours(args) -> None:
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"rhs_saturated_{n}^3_fp64", "grid": [n] * 3, "halo": 2, "gamma": 1.4, "eps": 0.25,
-                   "tile": tile_text(tuned_tile) + ("" if args.tile else " (acs_autotune_rhs)"), "l2": f"inputs larger than L2 ({in_bytes / 1e6:.0f} MB in, {out_bytes / 1e6:.0f} MB out)",
-                   "parallelism": f"replicas x{world}"},
+        "config": workload_config(n, world),
+        "form": "saturated", "tile": tile_text(tuned_tile) + ("" if args.tile else " (acs_autotune_rhs)"),
         "roofline": {"bound": "alu", "achieved": achieved_ops, "peak": peak, "unit": "G FP64-pipe op/s",
                      "frac": achieved_ops / peak, "traffic": traffic,
                      "peak_source": "measured in this run: acs_fp64_rate_probe, register-only FP64 FMA chains at "

@@ -10,6 +10,8 @@ import sys
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
 
 
 def _run(args, timeout):
@@ -28,7 +30,7 @@ def test_reference_arm_line():
     assert d["steps"] == 3 and d["warmup"] == 3 and d["ms_per_step"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
-    assert d["config"]["workload"].startswith("rhs_as_written_oracle_256")
+    assert d["config"] == bench.workload_config(256, 1)
 
 
 @pytest.mark.gpu
@@ -38,7 +40,7 @@ def test_default_arm_line():
                 "vs_baseline", "dtype", "data", "config", "roofline", "e2e", "gpu_launches", "clocks"):
         assert key in d, key
     assert d["n_gpus"] == 1 and d["steps"] == 5 and d["warmup"] == 3 and d["dtype"] == "f64"
-    assert d["config"]["workload"] == "rhs_saturated_256^3_fp64" and "l2" in d["config"]
+    assert d["config"] == bench.workload_config(256, 1) and d["form"] == "saturated"
     r = d["roofline"]
     assert r["bound"] == "alu" and 0 < r["frac"] <= 1.05 and r["achieved"] == pytest.approx(r["frac"] * r["peak"])
     assert d["gpu_launches"] == 5
