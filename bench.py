@@ -262,8 +262,44 @@ def cpu_baseline(U: np.ndarray, budget_s: float = 10.0) -> dict:
         dt += time.perf_counter() - t
         pts += n ** 3
         passes += 1
+    # the same oracle on one thread, over whole z-planes for about 2 s
+    one = {"value": None, "planes": 0}
+    if threads > 1:
+        planes, t1s = 0, 0.0
+        while t1s < 2.0 and planes < n:
+            t = time.perf_counter()
+            oracle.rhs(U, k_range=(planes, planes + 1), threads=1)
+            t1s += time.perf_counter() - t
+            planes += 1
+        one = {"value": planes * n * n / t1s / 1e9, "planes": planes}
     return {"value": pts / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"as-written RHS oracle, {passes} passes over the whole {n}^3 field ({pts} points, {dt:.1f} s)"}
+            "sample": f"as-written RHS oracle, {passes} passes over the whole {n}^3 field ({pts} points, {dt:.1f} s)",
+            "host_cpu": cpu_model(), "single_thread_value": one["value"],
+            "single_thread_sample": f"{one['planes']} z-planes of the same field on one core"}
+
+
+def cpu_model() -> str:
+    """The host CPU as the OS names it (model name, or the implementer and part on Arm)."""
+    import platform
+    name, impl, part = None, None, None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                k, v = k.strip().lower(), v.strip()
+                if k == "model name" and not name:
+                    name = v
+                elif k == "cpu implementer" and not impl:
+                    impl = v
+                elif k == "cpu part" and not part:
+                    part = v
+    except OSError:
+        pass
+    if name:
+        return f"{name} ({platform.machine()})"
+    if impl or part:
+        return f"{platform.machine()} implementer {impl} part {part}"
+    return platform.machine() or "unknown"
 
 
 def run_reference(args) -> None:
@@ -301,7 +337,8 @@ def run_reference(args) -> None:
         "config": workload_config(N_RHS, args.gpus),
         "form": "as written, the CPU oracle (plain C, FP64, no FMA contraction)",
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"{planes} z-planes of the {N_RHS}^3 field per step ({pts} points)"},
+                         "sample": f"{planes} z-planes of the {N_RHS}^3 field per step ({pts} points)",
+                         "host_cpu": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
