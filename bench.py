@@ -573,7 +573,7 @@ def bench_ranker(binding, ranker, n_variants: int = 512) -> dict:
     paper's analytical cost), every variant checked against the library's saturated kernel."""
     t = time.time()
     res = ranker.study(n_variants=n_variants, n=N_RHS, epochs=2000, reps=3, scope=binding.SCOPE_MARCH,
-                       extra_splits=20)
+                       extra_splits=20, search_candidates=2048)
     res["wall_s"] = time.time() - t
     return res
 
@@ -970,7 +970,7 @@ def run_ours(args) -> None:
                 "spearman_analytical_test", "best_test_ms", "mlp_pick_ms", "analytical_pick_ms", "mlp_pick_over_best",
                 "analytical_pick_over_best", "all_ms_min", "all_ms_median", "all_ms_max",
                 "max_err_over_tol_vs_saturated", "mlp_pick_index", "mlp_pick_shape", "best_all_index",
-                "mlp_top3_measured_over_best", "splits",
+                "mlp_top3_measured_over_best", "search", "splits",
                 "wall_s")
         result["ranker"] = {"workload": f"march-scope rewriter variants of the RHS at {N_RHS}^3",
                             **{k: study[k] for k in keys},

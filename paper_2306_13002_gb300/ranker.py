@@ -36,16 +36,22 @@ def spearman(a, b) -> float:
     return float((ra * rb).sum() / den) if den > 0 else 0.0
 
 
-def generate(n: int, seed: int = inputs.SEED_VARIANTS, scope: int = binding.SCOPE_MARCH):
-    """Host rewriter output for variants 0..n-1 of `scope`: list of dicts (src, dag, feats, ...)."""
-    out = []
-    for i in range(n):
-        src, dag, info = binding.acs_variant_generate(seed, i, scope)
-        out.append({"index": i, "src": src, "dag": dag, "info": info,
-                    "feats": np.array(info.feats[:], dtype=np.float32), "cost": info.cost,
-                    "block": (info.block_x, info.block_y), "flags": info.flags, "enodes": info.enodes,
-                    "iterations": info.iterations})
-    return out
+def _one(seed: int, i: int, scope: int) -> dict:
+    src, dag, info = binding.acs_variant_generate(seed, i, scope)
+    return {"index": i, "src": src, "dag": dag, "info": info,
+            "feats": np.array(info.feats[:], dtype=np.float32), "cost": info.cost,
+            "block": (info.block_x, info.block_y), "flags": info.flags, "enodes": info.enodes,
+            "iterations": info.iterations}
+
+
+def generate(n: int, seed: int = inputs.SEED_VARIANTS, scope: int = binding.SCOPE_MARCH, start: int = 0,
+             threads: int | None = None):
+    """Host rewriter output for variants start..start+n-1 of `scope`: list of dicts (src, dag,
+    feats, ...) in index order. Generation is host code with no shared state, run on `threads`
+    threads (the library call releases the interpreter lock)."""
+    threads = threads or min(16, os.cpu_count() or 4)
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        return list(ex.map(lambda i: _one(seed, i, scope), range(start, start + n)))
 
 
 def distinct(variants):
@@ -101,6 +107,49 @@ def max_err_over_tol(R, ref, tol=None) -> float:
     return float((R - ref).abs_().div_(tol).max())
 
 
+def search(params, hidden: int, start: int, count: int, U, R, regs_fill: float, known: set | None = None,
+           seed: int = inputs.SEED_VARIANTS, shortlist: int = 64, timed: int = 8, reps: int = 3) -> dict:
+    """The trained MLP as the cost model of a wider search: rewriter variants start..start+count-1
+    (march scope) are generated on the host and ranked without compiling them (their register
+    count, known only after compilation, set to `regs_fill`); the first `shortlist` are compiled,
+    re-ranked with their real register counts, and the first `timed` of those timed at U's size
+    and checked against the library's saturated kernel. `known` holds sources already measured
+    (skipped). Returns the timed candidates and the fastest."""
+    import torch
+    vs = [v for v in distinct(generate(count, seed, binding.SCOPE_MARCH, start=start))
+          if not known or v["src"] not in known]
+    reg_idx = binding.acs_variant_feature_names().index("regs")
+    for v in vs:
+        v["feats"][reg_idx] = regs_fill
+    X = torch.from_numpy(np.stack([v["feats"] for v in vs])).cuda()
+    order, _ = binding.acs_variant_rank(X, params, hidden)
+    short = [vs[i] for i in order[:shortlist]]
+    compile_all(short)
+    X2 = torch.from_numpy(np.stack([v["feats"] for v in short])).cuda()
+    order2, pred2 = binding.acs_variant_rank(X2, params, hidden)
+    top = [short[i] for i in order2[:timed]]
+    for v in short:
+        if not any(v is t for t in top):
+            v["module"].close()
+    time_all(top, U, R, reps=reps)
+    ref = torch.empty_like(R)
+    binding.acs_rhs_saturated(U, ref)
+    tol = ref.abs().mul_(1e-12).add_(1e-14)
+    worst = 0.0
+    for v in top:
+        R.fill_(float("nan"))
+        v["module"].launch(U, R)
+        worst = max(worst, max_err_over_tol(R, ref, tol))
+        v["module"].close()
+    del ref, tol
+    best = min(top, key=lambda v: v["ms"])
+    return {"candidates": count, "distinct_new": len(vs), "shortlist": len(short), "timed": len(top),
+            "timed_ms": [round(float(v["ms"]), 4) for v in top],
+            "predicted_ms_first": float(pred2[order2[0]]),
+            "best_index": int(best["index"]), "best_ms": float(best["ms"]),
+            "best_shape": [*best["block"], best["flags"]], "max_err_over_tol_vs_saturated": worst}
+
+
 # Model-guided selection: the MLP's first TOP_K variants are timed and the fastest is kept (the
 # study has every variant's time already and reads it off). The MLP's first choice alone is the
 # pure model pick; a few timings cover its near-ties and the rare fast variant unlike the
@@ -111,14 +160,16 @@ TOP_K = 3
 def study(n_variants: int = 512, n_train: int | None = None, n: int = 256, seed: int = inputs.SEED_VARIANTS,
           hidden: int = 64, epochs: int = 3000, lr: float = 3e-3, reps: int = 5,
           scope: int = binding.SCOPE_MARCH, check: bool = True, fast_weight: float = 1.0,
-          extra_splits: int = 0) -> dict:
+          extra_splits: int = 0, search_candidates: int = 0) -> dict:
     """Generate `n_variants` variants, keep the distinct ones, compile and time them at n^3, train the
     MLP on a random n_train of them (default: 400/512 of the distinct variants; squared error of the
     standardised log time weighted by exp(-fast_weight t), so the fast variants that decide the
     pick weigh more) and rank the rest, by the MLP and by the paper's analytical cost. With `check`, every variant's output is compared
     with the library's saturated kernel (itself parity-checked against the oracle) at n^3.
     `extra_splits` more random train/test splits (seeds seed + 1 ...) of the same timed variants are
-    trained and ranked the same way; their MLP pick / best ratios are summarised in "splits"."""
+    trained and ranked the same way; their MLP pick / best ratios are summarised in "splits".
+    With `search_candidates`, the model trained on the first split then searches that many further
+    variants (`search`, indices n_variants onwards); the result is in "search"."""
     import torch
     vs_all = generate(n_variants, seed, scope)
     vs = distinct(vs_all)
@@ -170,6 +221,13 @@ def study(n_variants: int = 512, n_train: int | None = None, n: int = 256, seed:
     pick_m = float(times_te[order_m[0]])
     pick_a = float(times_te[order_a[0]])
     all_ms = np.array([v["ms"] for v in vs])
+    found = None
+    if search_candidates > 0:
+        regs_idx = binding.acs_variant_feature_names().index("regs")
+        found = search(params, hidden, n_variants, search_candidates, U, R,
+                       float(np.median([v["feats"][regs_idx] for v in vs])), known={v["src"] for v in vs_all},
+                       seed=seed)
+        found["best_over_study_best"] = found["best_ms"] / float(all_ms.min())
     ratios, ratios_k = [], []
     for sp in range(1, extra_splits + 1):
         p2 = np.random.default_rng(seed + sp).permutation(nd)
@@ -200,6 +258,7 @@ def study(n_variants: int = 512, n_train: int | None = None, n: int = 256, seed:
         "best_test_index": int(pb["index"]),
         "mlp_pick_shape": [*pm["block"], pm["flags"]],
         "best_all_index": int(vs[int(np.argmin(all_ms))]["index"]),
+        "search": found,
         "splits": None if not ratios else {
             "n": len(ratios), "seeds": [seed + 1, seed + len(ratios)],
             "mlp_pick_within_5pct_of_best": int(sum(r <= 1.05 for r in ratios)),

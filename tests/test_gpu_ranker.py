@@ -162,13 +162,17 @@ def test_small_study_end_to_end():
     """The whole pipeline on 64 march variants at 64^3: distinct variants only, split without
     duplicates, every variant consistent with the library's saturated kernel, and the MLP's pick
     among the held-out variants within 15 % of the best of them (the bench reports the 256^3 study)."""
-    res = ranker.study(n_variants=64, n=64, epochs=1500, reps=3, extra_splits=3)
+    res = ranker.study(n_variants=64, n=64, epochs=1500, reps=3, extra_splits=3, search_candidates=48)
     assert res["variants_distinct"] >= 56 and res["train"] + res["test"] == res["variants_distinct"]
     sp = res["splits"]
     assert sp["n"] == 3 and 0 <= sp["mlp_pick_within_5pct_of_best"] <= 3
     assert 1.0 <= sp["mlp_pick_over_best_mean"] <= sp["mlp_pick_over_best_worst"]
     assert 1.0 <= sp["mlp_top3_measured_over_best_worst"] <= sp["mlp_pick_over_best_worst"]
     assert 1.0 <= res["mlp_top3_measured_over_best"] <= res["mlp_pick_over_best"]
+    se = res["search"]   # the model ranks 48 further variants, compiles its shortlist, times the first 8
+    assert se["candidates"] == 48 and 1 <= se["timed"] <= 8 and se["timed"] <= se["shortlist"] <= se["distinct_new"]
+    assert se["best_ms"] == pytest.approx(min(se["timed_ms"]), abs=1e-4) and se["best_index"] >= 64
+    assert se["max_err_over_tol_vs_saturated"] <= 2.0
     assert res["max_err_over_tol_vs_saturated"] <= 2.0
     assert res["best_test_ms"] > 0
     assert res["mlp_pick_over_best"] <= 1.15, res
