@@ -97,7 +97,11 @@ __global__ void __launch_bounds__(BX * BY, KIND == ACS_KIND_RHS ? RhsShape<BX, B
         const int k0 = kc * d.kchunk;
         const int k1 = min(k0 + d.kchunk, d.g.nz);
         if (KIND == ACS_KIND_RHS) {
-            rhs_march<BX, BY, false>(d.in0, d.out, d.g, rk, tx * BX, ty * BY, k0, k1, smem, nullptr, nullptr);
+            if (rhs_isotropic(rk))   // uniform over the launch: the batch shares one set of constants
+                rhs_march<BX, BY, false, true>(d.in0, d.out, d.g, rk, tx * BX, ty * BY, k0, k1, smem, nullptr, nullptr);
+            else
+                rhs_march<BX, BY, false, false>(d.in0, d.out, d.g, rk, tx * BX, ty * BY, k0, k1, smem, nullptr,
+                                                nullptr);
         } else if (d.tma) {
             const CUtensorMap* map = reinterpret_cast<const CUtensorMap*>(ws + h->maps_off) + it;
             if (leader) tensormap_acquire(map);

@@ -41,6 +41,16 @@ struct RhsRegs {
 // sum m v' = s |m|^2/rho with the folded constant nhg1 / s. Two more operations per point,
 // four fewer per point in the combine (one per flux component). Distributivity and constant
 // folding: the same value up to rounding.
+// Whether a launch with constants k takes the form with the scale folded into the fluxes: equal
+// spacing on the three axes, with |s| within 2^-64 .. 2^64. The folded flux values carry the
+// factor s, so their exponents move by log2 |s|, while the three-scale form's flux values do not
+// depend on h at all; the range keeps that shift small against the exponent range. Other
+// spacings run the three-scale form.
+__host__ __device__ inline bool rhs_isotropic(const RhsConst& k) {
+    const double as = fabs(k.sx);
+    return k.sx == k.sy && k.sy == k.sz && as >= 0x1p-64 && as <= 0x1p64;
+}
+
 template <bool ISO = false>
 __device__ __forceinline__ void point_flux(double rho, double mx, double my, double mz, double E, const RhsConst& k,
                                            double fx[4], double fy[4], double fz[4]) {

@@ -110,13 +110,9 @@ acs_status launch_t(const double* U, double* R, const Geom& g, const RhsConst& k
     memset(&map, 0, sizeof(map));
     // TMA staging where the layout allows it (the box: the tile plus its 2-cell halo, one
     // plane, all five components of the halo-extended U); element-wise staging otherwise.
-    // Equal spacing on the three axes selects the form with the scale folded into the fluxes.
-    // Its flux values carry the factor s, so their exponents move by log2 |s|, while the
-    // three-scale form's flux values do not depend on h at all. The fold is therefore taken only
-    // for |s| within 2^-64 .. 2^64 (spacings of about 2^-65 .. 2^63), which keeps that shift
-    // small against the exponent range; other spacings run the three-scale form.
-    const double as = fabs(k.sx);
-    const bool iso = k.sx == k.sy && k.sy == k.sz && as >= 0x1p-64 && as <= 0x1p64;
+    // Equal spacing on the three axes (within 2^-65 .. 2^63) selects the form with the scale
+    // folded into the fluxes (rhs_isotropic).
+    const bool iso = rhs_isotropic(k);
     if ((flags & ACS_TILE_TMA) && encode_plane_map(U, g, 5, BX + 4, BY + 4, &map) == ACS_OK)
         return iso ? launch_tt<BX, BY, true, true>(U, R, g, k, kchunk, flags, map, s)
                    : launch_tt<BX, BY, true, false>(U, R, g, k, kchunk, flags, map, s);

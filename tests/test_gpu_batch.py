@@ -50,8 +50,9 @@ def test_stencil_batch_tiles(tile):
         assert_parity(out.cpu().numpy(), oracle.stencil(u, a), what=f"batch {tile} grid {u.shape}")
 
 
+@pytest.mark.parametrize("h", [(1.0, 0.5, 2.0), (0.37, 0.37, 0.37)])   # three scales / folded into the fluxes
 @pytest.mark.parametrize("tile", [None, (16, 8, 4), (32, 16, 8)])
-def test_rhs_batch_matches_oracle(tile):
+def test_rhs_batch_matches_oracle(tile, h):
     rng = np.random.default_rng(11)
     sides = rng.integers(1, 60, size=(10, 3))
     grids, host = [], []
@@ -60,12 +61,12 @@ def test_rhs_batch_matches_oracle(tile):
         R = torch.full((5, int(nz), int(ny), int(nx)), float("nan"), dtype=torch.float64, device="cuda")
         grids.append((to_dev(U), None, R))
         host.append(U)
-    params = {"gamma": 1.4, "eps": 0.25, "h": (1.0, 0.5, 2.0)}
+    params = {"gamma": 1.4, "eps": 0.25, "h": h}
     plan = binding.acs_batch_prepare(binding.KIND_RHS, grids, _ws(len(grids)), tile=tile)
     binding.acs_batch_launch(plan, params)
     torch.cuda.synchronize()
     for U, (_, _, R) in zip(host, grids):
-        assert_parity(R.cpu().numpy(), oracle.rhs(U, h=(1.0, 0.5, 2.0)), what=f"rhs batch {U.shape}")
+        assert_parity(R.cpu().numpy(), oracle.rhs(U, h=h), what=f"rhs batch {U.shape} h={h}")
 
 
 def _guided_units(sides, bx, by, kchunk, per_sm):
