@@ -57,8 +57,8 @@ FALLBACK_SM_MAX_MHZ = 2070.0
 NCU_TRAFFIC = {
     # one-pass ncu captures (dram__bytes_read.sum + dram__bytes_write.sum) of one launch at
     # 256^3, the 4th after 3 warm-ups, in the shapes the autotuner picks
-    "bf9c1163e10c111a:16x16, balanced, TMA": 830774016 + 633936384,
-    "bf9c1163e10c111a:32x8, balanced, TMA": 858266368 + 633995520,
+    "cd1a3ed280707f36:16x16, balanced, TMA": 830774016 + 633936384,
+    "cd1a3ed280707f36:32x8, balanced, TMA": 858266368 + 633995520,
 }
 
 
