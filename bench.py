@@ -14,6 +14,7 @@ over ranks (each rank runs its own replica: no collective on the data path).
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -476,13 +477,21 @@ def time_launches(torch, fn, steps: int, stream, per=None) -> tuple[float, float
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    r0.record(stream)
-    for s in range(steps):
-        starts[s].record(stream)
-        fn()
-        ends[s].record(stream)
-    r1.record(stream)
-    torch.cuda.synchronize()
+    # no garbage collection while the steps are enqueued (as timeit does): a collection pause in
+    # the enqueue loop would leave the GPU idle between steps and be timed as part of a step
+    gc_on = gc.isenabled()
+    gc.disable()
+    try:
+        r0.record(stream)
+        for s in range(steps):
+            starts[s].record(stream)
+            fn()
+            ends[s].record(stream)
+        r1.record(stream)
+        torch.cuda.synchronize()
+    finally:
+        if gc_on:
+            gc.enable()
     durations = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     if per is not None:
         per.extend(durations)
