@@ -971,7 +971,11 @@ def run_ours(args) -> None:
     }
     if not args.no_stencil:
         result["block_128"] = bench_block(torch, binding, inputs, stream, max(3, min(args.steps, 20)))
-    if not args.no_ranker:
+    # The ranker study, the large workloads and the CPU baseline are single-GPU studies that rank 0
+    # would run while the other ranks' GPUs stay held: the N = 1 line carries them.
+    if world > 1:
+        result["single_gpu_blocks"] = "ranker, large and cpu_baseline are reported at N = 1 only"
+    if not args.no_ranker and world == 1:
         from paper_2306_13002_gb300 import ranker
         torch.cuda.empty_cache()
         study = bench_ranker(binding, ranker)
@@ -988,7 +992,7 @@ def run_ours(args) -> None:
         if not args.no_large:
             result["large"] = bench_large(torch, binding, inputs, stream, peak, study["mlp_pick_index"],
                                           max(3, min(args.steps, 10)))
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:
         result["cpu_baseline"] = cpu_baseline(U_host)
     print(json.dumps(result))
     if dist:
