@@ -582,7 +582,7 @@ def bench_ranker(binding, ranker, n_variants: int = 512) -> dict:
     ones among `n_variants` rewriter variants (78 % train, the rest ranked by the MLP and by the
     paper's analytical cost), every variant checked against the library's saturated kernel."""
     t = time.time()
-    res = ranker.study(n_variants=n_variants, n=N_RHS, epochs=2000, reps=3, scope=binding.SCOPE_MARCH,
+    res = ranker.study(n_variants=n_variants, n=N_RHS, epochs=2000, reps=5, scope=binding.SCOPE_MARCH,
                        extra_splits=20, search_candidates=2048)
     res["wall_s"] = time.time() - t
     return res
