@@ -81,10 +81,12 @@ class Oracle:
         return bool(self.lib.oracle_has_openmp())
 
     def rhs(self, U: np.ndarray, gamma: float = 1.4, eps: float = 0.25, h=(1.0, 1.0, 1.0), halo: int = 2,
-            k_range: tuple[int, int] | None = None, threads: int = 1) -> np.ndarray:
+            k_range: tuple[int, int] | None = None, threads: int = 1, out: np.ndarray | None = None) -> np.ndarray:
         """As-written RHS. U: (5, nz+2h, ny+2h, nx+2h) float64 (any row/plane pitch).
 
-        Returns R: (5, nz, ny, nx); planes outside `k_range` are left as NaN.
+        Returns R: (5, nz, ny, nx); planes outside `k_range` are left as NaN. With `out` (a
+        C-contiguous float64 array of that shape, reused across calls) R is written there instead
+        of a new NaN-filled array, and planes outside `k_range` keep what `out` held.
         """
         if U.ndim != 4 or U.shape[0] != 5:
             raise ValueError("U must be (5, Z, Y, X)")
@@ -92,7 +94,12 @@ class Oracle:
             raise ValueError("the RHS needs a halo of at least 2")
         nz, ny, nx = (s - 2 * halo for s in U.shape[1:])
         sc, sz, sy, _ = _strides(U)
-        R = np.full((5, nz, ny, nx), np.nan)
+        if out is None:
+            R = np.full((5, nz, ny, nx), np.nan)
+        else:
+            if out.shape != (5, nz, ny, nx) or out.dtype != np.float64 or not out.flags["C_CONTIGUOUS"]:
+                raise ValueError("out must be a C-contiguous float64 array of shape (5, nz, ny, nx)")
+            R = out
         k0, k1 = (0, nz) if k_range is None else k_range
         self.lib.oracle_rhs(U.ctypes.data, R.ctypes.data, nx, ny, nz, halo, sy, sz, sc,
                             nx, nx * ny, nx * ny * nz, float(gamma), float(eps),
@@ -166,9 +173,9 @@ def has_openmp() -> bool:
     return default().has_openmp()
 
 
-def rhs(U, gamma=1.4, eps=0.25, h=(1.0, 1.0, 1.0), halo=2, k_range=None, threads=1):
+def rhs(U, gamma=1.4, eps=0.25, h=(1.0, 1.0, 1.0), halo=2, k_range=None, threads=1, out=None):
     """As-written RHS through the default oracle build (see `Oracle.rhs`)."""
-    return default().rhs(U, gamma, eps, h, halo, k_range, threads)
+    return default().rhs(U, gamma, eps, h, halo, k_range, threads, out)
 
 
 def block(A, B, G, prm=(0.01, 1.5, 2.0, 0.75, 0.5), halo=1, k_range=None, threads=1):
