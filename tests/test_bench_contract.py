@@ -55,3 +55,50 @@ def test_default_arm_line():
     link = e["host_link"]
     assert 0 < link["both_ms"] <= e["ms_per_step"] * 1.02
     assert link["upload_gbs"] > 50 and link["download_gbs"] > 50
+
+
+class _FakeNvml:
+    """Stands in for the NVML wrapper: fixed readings, counts the queries."""
+
+    def __init__(self):
+        self.calls = 0
+
+    def sm_mhz(self):
+        self.calls += 1
+        return 2070.0
+
+    def power_w(self):
+        return 300.0
+
+    def reasons(self):
+        return []
+
+
+def test_clock_sampler_windows_and_pause():
+    """The sampler keeps only samples inside registered windows, and queries nothing while paused."""
+    import time
+    sm = bench.ClockSampler(0, period_s=0.002)
+    sm.nvml, sm.max_mhz = _FakeNvml(), 2070.0
+    sm.start()
+    time.sleep(0.05)
+    sm.pause()
+    time.sleep(0.01)              # a query already under way may still land
+    n0 = sm.nvml.calls
+    time.sleep(0.05)
+    assert sm.nvml.calls == n0    # no queries while paused
+    sm.resume()
+    t0 = time.time()
+    time.sleep(0.05)
+    t1 = time.time()
+    sm.window(t0, t1)
+    sm.stop()
+    s = sm.summary()
+    assert s["samples"] >= 5 and s["sm_mhz"] == 2070.0 and s["reasons"] == []
+    assert all(t0 <= r[0] <= t1 for r in sm.samples if t0 <= r[0] <= t1)
+    assert s["samples"] < len(sm.samples)   # samples outside the window are not counted
+
+
+def test_workload_config_is_shared_by_both_arms():
+    c = bench.workload_config(256, 1)
+    assert c["workload"] == "rhs_256^3_fp64" and c["grid"] == [256] * 3 and c["h"] == [1.0, 1.0, 1.0]
+    assert "703 MB in, 671 MB out" in c["l2"] and c["parallelism"] == "replicas x1"
