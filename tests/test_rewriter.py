@@ -234,3 +234,14 @@ def test_march_variants_are_diverse_and_compile_on_the_host():
     for src, _, info in infos[1:6]:
         assert binding.lib().acs_variant_build(src.encode(), ctypes.byref(info), None, None) == 0, \
             binding.lib().acs_last_error().decode()
+
+
+def test_threaded_generation_matches_one_at_a_time():
+    """ranker.generate runs the host rewriter on several threads; the variants, their order and
+    their features equal those of one-at-a-time calls (the rewriter keeps no shared state)."""
+    par = ranker.generate(24, inputs.SEED_VARIANTS, binding.SCOPE_MARCH, start=500, threads=8)
+    for v in par:
+        src, dag, info = binding.acs_variant_generate(inputs.SEED_VARIANTS, v["index"], binding.SCOPE_MARCH)
+        assert v["src"] == src and v["dag"] == dag
+        assert np.array_equal(v["feats"], np.array(info.feats[:], dtype=np.float32))
+    assert [v["index"] for v in par] == list(range(500, 524))
