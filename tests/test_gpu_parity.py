@@ -442,23 +442,25 @@ def test_block_forms_halo2_padded(form):
 
 # ----------------------------------------------------------- streamed host-buffer RHS
 
+@pytest.mark.parametrize("h", [(1.0, 0.5, 2.0), (0.37, 0.37, 0.37)])   # three scales / folded into the fluxes
 @pytest.mark.parametrize("dims,slab", [((37, 29, 71), 16), ((20, 9, 5), 32), ((33, 17, 64), 32), ((8, 8, 1), 0),
-                                       ((19, 7, 21), 1), ((19, 7, 23), 3), ((24, 10, 41), 16), ((24, 10, 40), 16)])
-def test_rhs_saturated_host_streamed(dims, slab):
+                                       ((19, 7, 21), 1), ((19, 7, 23), 3), ((24, 10, 41), 16), ((24, 10, 40), 16),
+                                       ((21, 11, 90), 0)])
+def test_rhs_saturated_host_streamed(dims, slab, h):
     nx, ny, nz = dims
     U = inputs.rhs_field(nx, ny, nz, halo=2, seed=6500 + nz)
-    ref = oracle.rhs(U, h=(1.0, 0.5, 2.0))
+    ref = oracle.rhs(U, h=h)
     Uh = torch.from_numpy(U).pin_memory()
     Rh = torch.full((5, nz, ny, nx), float("nan"), dtype=torch.float64).pin_memory()
     nb = binding.acs_rhs_host_workspace_bytes(Uh, Rh, slab=slab)
     ws = torch.empty(nb // 8 + 2, dtype=torch.float64, device="cuda")
     s = torch.cuda.current_stream()
-    binding.acs_rhs_saturated_host(Uh, Rh, ws, h=(1.0, 0.5, 2.0), slab=slab, stream=s)
+    binding.acs_rhs_saturated_host(Uh, Rh, ws, h=h, slab=slab, stream=s)
     s.synchronize()
-    assert_parity(Rh.numpy(), ref, what=f"host streamed {dims} slab {slab}")
+    assert_parity(Rh.numpy(), ref, what=f"host streamed {dims} slab {slab} h={h}")
     # a second call on the same workspace (buffers reused in the other order) gives the same bits
     R2 = torch.full_like(Rh, float("nan")).pin_memory()
-    binding.acs_rhs_saturated_host(Uh, R2, ws, h=(1.0, 0.5, 2.0), slab=slab, stream=s)
+    binding.acs_rhs_saturated_host(Uh, R2, ws, h=h, slab=slab, stream=s)
     s.synchronize()
     assert torch.equal(R2, Rh)
 
